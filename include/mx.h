@@ -1,0 +1,194 @@
+/*
+ * mx.h -- C ABI of libmx, a GB300 (sm_103a) implementation of the per-stage
+ * hot path of the micromagnetics method of MagneX (arXiv 2602.12242):
+ * effective field H_eff = H_bias + H_demag + H_ani + H_exch + H_DMI (Eq. 2),
+ * the Landau-Lifshitz-Gilbert right-hand side (Eq. 1) and explicit time
+ * stepping (classical RK4, forward Euler) with renormalisation |m| = 1
+ * after every stage (Sec. II-B).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: nx * ny * nz cells of dx * dy * dz (metres), cell (i, j, k) at flat
+ *   index c = i + nx * (j + ny * k).
+ * Vector fields (m, H, dm/dt): DEVICE pointers to nx*ny*nz float4 records
+ *   (x, y, z, unused), 16-byte aligned, FP32, SI units (H in A/m, dm/dt in
+ *   1/s).  m is the unit magnetisation M / Ms.
+ * Scalar maps: DEVICE pointers to nx*ny*nz floats.
+ * Ownership: the caller owns every pointer it passes; the context owns its
+ *   own workspaces (demag spectra, stage buffers) and frees them in
+ *   mx_destroy.  No entry point keeps a caller pointer after it returns,
+ *   except that a CUDA graph captured by mx_rk_step for a given m pointer is
+ *   reused while the same pointer, dt and method come back.
+ * Streams: every call that takes a stream enqueues its work on that stream
+ *   and returns without waiting, unless its comment says it synchronises.
+ *   A NULL stream is the legacy default stream.
+ * Errors: every call returns an mx_status; MX_OK is 0.  On failure a message
+ *   is kept per host thread and mx_last_error() returns it.  No call aborts,
+ *   traps on the device or throws across the ABI.  A context is not
+ *   thread-safe: one host thread at a time.
+ * Device: a context lives on the CUDA device that is current when
+ *   mx_create is called; every later call must run with that device current.
+ */
+#ifndef MX_H
+#define MX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mx_stream_t; /* same type as cudaStream_t */
+typedef struct mx_ctx mx_ctx;
+
+typedef enum {
+    MX_OK = 0,
+    MX_ERR_INVALID_ARG = 1, /* bad size, NULL or misaligned pointer, bad flag   */
+    MX_ERR_CUDA = 2,        /* a CUDA runtime call failed (message has details) */
+    MX_ERR_OOM = 3,         /* a workspace allocation failed                     */
+    MX_ERR_NOT_BUILT = 4,   /* demag needed but mx_build_demag_kernel not run    */
+    MX_ERR_NONFINITE = 5,   /* a NaN/Inf was produced (reported by mx_sync)      */
+    MX_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                     */
+    MX_ERR_UNSUPPORTED = 7  /* size or option outside what this build supports   */
+} mx_status;
+
+/* Physical and numerical parameters (SI units).
+ *   Ms      saturation magnetisation [A/m] (used where no Ms map is set)
+ *   A       exchange stiffness [J/m]                  (Sec. II-A, exchange)
+ *   Ku      uniaxial anisotropy constant [J/m^3]      (Sec. II-A, anisotropy)
+ *   D       interfacial DMI constant [J/m^2]          (Sec. II-A, DMI)
+ *   alpha   Gilbert damping                           (Eq. 1)
+ *   gamma   gamma0 = mu0 |gamma| [m/(A s)], e.g. 2.211e5 (Eq. 1 with
+ *           gamma = -1.759e11 C/kg)
+ *   ku_axis easy axis (normalised internally) where no axis map is set
+ *   h_bias  constant applied field [A/m]
+ *   dmi_interfacial  1: interfacial DMI field and the chiral boundary
+ *           condition dm/dx_k = -(D/2A)(e_z x e_k) x m (Sec. II-A, II-B);
+ *           0: no DMI, Neumann boundaries
+ *   precession 1: full LLG; 0: damping term only (relaxation)
+ *   demag   1: include the demagnetising field
+ */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double Ms, A, Ku, D, alpha, gamma;
+    double ku_axis[3];
+    double h_bias[3];
+    int dmi_interfacial;
+    int precession;
+    int demag;
+} mx_params;
+
+/* Field terms, for mx_heff's term mask. */
+enum {
+    MX_TERM_DEMAG = 1,
+    MX_TERM_EXCH = 2,
+    MX_TERM_ANIS = 4,
+    MX_TERM_DMI = 8,
+    MX_TERM_ZEEMAN = 16,
+    MX_TERM_ALL = 31
+};
+
+/* Integrators for mx_rk_step. */
+enum { MX_RK4 = 0, MX_EULER = 1 };
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *mx_last_error(void);
+
+/* Version string of this build. */
+const char *mx_version(void);
+
+/* Create a context for the grid and parameters in *p on the current device.
+ * Allocates every workspace the hot path needs (no allocation happens
+ * later).  Sizes: 1 <= nx, ny <= 2048, 1 <= nz <= 2048; the padded grid
+ * (smallest power of two >= 2n-1 per axis of n > 1, else 1) must satisfy
+ * Px, Py, Pz <= 4096.  Cell sizes, Ms, A must be > 0 (A may be 0 when D is
+ * 0), alpha >= 0, gamma > 0.  *out receives the context, NULL on failure.
+ * Errors: MX_ERR_INVALID_ARG, MX_ERR_UNSUPPORTED, MX_ERR_OOM, MX_ERR_CUDA. */
+mx_status mx_create(mx_ctx **out, const mx_params *p);
+
+/* Free every workspace and the context.  NULL is accepted. */
+mx_status mx_destroy(mx_ctx *ctx);
+
+/* Per-cell saturation magnetisation [A/m] (nx*ny*nz floats, all > 0), copied
+ * into the context on `stream` (the caller may free its buffer after the
+ * stream reaches this point).  NULL reverts to the scalar p->Ms.  The demag
+ * field uses M = Ms_i m_i, the exchange/DMI/anisotropy fields divide by Ms_i. */
+mx_status mx_set_ms_map(mx_ctx *ctx, const float *ms_dev, mx_stream_t stream);
+
+/* Per-cell anisotropy: ku_dev nx*ny*nz floats [J/m^3] and axis_dev
+ * nx*ny*nz float4 unit axes, copied into the context on `stream`.  Either
+ * may be NULL to use the scalar value of p. */
+mx_status mx_set_anis_map(mx_ctx *ctx, const float *ku_dev, const float *axis_dev,
+                          mx_stream_t stream);
+
+/* Replace the constant applied field [A/m] (host array of 3 doubles).
+ * Takes effect for work enqueued after this call. */
+mx_status mx_set_bias(mx_ctx *ctx, const double h[3]);
+
+/* Build the demag kernel for this grid (Sec. II-B: the tensor of Newell et
+ * al. on the zero-padded grid, then its FFT): real-space tensor in FP64
+ * (closed form near, Gauss-Legendre quadrature of the defining integral
+ * far), FP64 FFT, the real spectrum scaled by -1/(Px Py Pz) and stored in
+ * FP32 as one octant per component.  Enqueued on `stream`; synchronises
+ * `stream` before returning (it frees its FP64 scratch). */
+mx_status mx_build_demag_kernel(mx_ctx *ctx, mx_stream_t stream);
+
+/* Effective field (Eq. 2) of m, restricted to the terms in `terms`
+ * (MX_TERM_* bits), written to h.  m and h must not overlap.
+ * MX_ERR_NOT_BUILT if the demag term is asked for before the kernel is built. */
+mx_status mx_heff(mx_ctx *ctx, const float *m, float *h, int terms, mx_stream_t stream);
+
+/* dm/dt of the LLG equation (Eq. 1 in m-form,
+ * dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)]) with the full
+ * H_eff of the context.  m and dmdt must not overlap. */
+mx_status mx_llg_rhs(mx_ctx *ctx, const float *m, float *dmdt, mx_stream_t stream);
+
+/* Advance m in place by nsteps steps of size dt [s] with MX_RK4 (four
+ * right-hand-side evaluations, every stage input and the result
+ * renormalised) or MX_EULER.  m is normalised on entry.  The first call for
+ * a given (m, dt, method, nsteps > 1) captures one step into a CUDA graph
+ * that later calls replay.  Non-finite values set a device flag that
+ * mx_sync reports. */
+mx_status mx_rk_step(mx_ctx *ctx, float *m, int nsteps, double dt, int method,
+                     mx_stream_t stream);
+
+/* Energies [J] of m: e_out[0..4] = demag, exchange, anisotropy, DMI,
+ * Zeeman (Sec. II-A energy densities: -mu0/2 Ms m.H_term for demag,
+ * exchange and DMI; Ku [1 - (e_K.m)^2]; -mu0 Ms m.H_bias), accumulated in
+ * FP64.  e_out is a HOST array.  Synchronises `stream`. */
+mx_status mx_energy(mx_ctx *ctx, const float *m, double e_out[5], mx_stream_t stream);
+
+/* Synchronise `stream`; return MX_ERR_NONFINITE (and clear the flag) if any
+ * kernel of this context produced a NaN or Inf since the last mx_sync. */
+mx_status mx_sync(mx_ctx *ctx, mx_stream_t stream);
+
+/* Padded grid of this context: out[0..2] = Px, Py, Pz. */
+mx_status mx_padded_dims(const mx_ctx *ctx, int out[3]);
+
+/* The FP64 real-space tensor on the non-negative offsets (X = i dx,
+ * Y = j dy, Z = k dz, 0 <= i < nx, 0 <= j < ny, 0 <= k < nz) as computed by
+ * the build, written to the DEVICE array out (6 * nz * ny * nx doubles,
+ * layout [c][k][j][i], c = xx, yy, zz, xy, xz, yz).  For checking the build. */
+mx_status mx_demag_tensor_real(mx_ctx *ctx, double *out, mx_stream_t stream);
+
+/* The stored FP32 spectrum octant, copied to the DEVICE array out
+ * (6 * (Pz/2+1) * (Py/2+1) * (Px/2+1) floats, layout [c][kz][ky][kx]),
+ * already scaled by -1/(Px Py Pz).  MX_ERR_NOT_BUILT before the build. */
+mx_status mx_demag_spectrum(mx_ctx *ctx, float *out, mx_stream_t stream);
+
+/* Kernel timing for profiling: runs `nsteps` steps exactly like
+ * mx_rk_step but launches every kernel directly (no graph) with a CUDA event
+ * pair around each launch, then synchronises.  For kernel index q in
+ * [0, *n_kernels), ms_total[q] and launches[q] receive the summed duration and
+ * the launch count; names via mx_kernel_name(q).  Arrays hold max_kernels. */
+mx_status mx_profile_step(mx_ctx *ctx, float *m, int nsteps, double dt, int method,
+                          mx_stream_t stream, double *ms_total, int *launches,
+                          int max_kernels, int *n_kernels);
+const char *mx_kernel_name(int q);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MX_H */

@@ -1,0 +1,174 @@
+"""ctypes binding of libmx (include/mx.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts
+arguments.  Loading fails loudly if ``_build/libmx.so`` is missing: there is
+no CPU fallback.
+
+Field tensors are torch CUDA float32 tensors of shape (nz, ny, nx, 4),
+contiguous (x, y, z, unused per cell); scalar maps are (nz, ny, nx) float32.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmx.so")
+
+MX_OK, MX_ERR_INVALID_ARG, MX_ERR_CUDA, MX_ERR_OOM, MX_ERR_NOT_BUILT, MX_ERR_NONFINITE, MX_ERR_TIMEOUT, \
+    MX_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = {0: "MX_OK", 1: "MX_ERR_INVALID_ARG", 2: "MX_ERR_CUDA", 3: "MX_ERR_OOM", 4: "MX_ERR_NOT_BUILT",
+                5: "MX_ERR_NONFINITE", 6: "MX_ERR_TIMEOUT", 7: "MX_ERR_UNSUPPORTED"}
+MX_TERM_DEMAG, MX_TERM_EXCH, MX_TERM_ANIS, MX_TERM_DMI, MX_TERM_ZEEMAN = 1, 2, 4, 8, 16
+MX_TERM_ALL = 31
+MX_RK4, MX_EULER = 0, 1
+
+
+class MxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mx_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("Ms", ctypes.c_double), ("A", ctypes.c_double), ("Ku", ctypes.c_double),
+                ("D", ctypes.c_double), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("ku_axis", ctypes.c_double * 3), ("h_bias", ctypes.c_double * 3),
+                ("dmi_interfacial", ctypes.c_int), ("precession", ctypes.c_int), ("demag", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "mx_last_error": (ctypes.c_char_p, []),
+    "mx_version": (ctypes.c_char_p, []),
+    "mx_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(mx_params)]),
+    "mx_destroy": (_I, [_P]),
+    "mx_set_ms_map": (_I, [_P, _P, _P]),
+    "mx_set_anis_map": (_I, [_P, _P, _P, _P]),
+    "mx_set_bias": (_I, [_P, ctypes.POINTER(_D)]),
+    "mx_build_demag_kernel": (_I, [_P, _P]),
+    "mx_heff": (_I, [_P, _P, _P, _I, _P]),
+    "mx_llg_rhs": (_I, [_P, _P, _P, _P]),
+    "mx_rk_step": (_I, [_P, _P, _I, _D, _I, _P]),
+    "mx_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
+    "mx_sync": (_I, [_P, _P]),
+    "mx_padded_dims": (_I, [_P, ctypes.POINTER(_I)]),
+    "mx_demag_tensor_real": (_I, [_P, _P, _P]),
+    "mx_demag_spectrum": (_I, [_P, _P, _P]),
+    "mx_profile_step": (_I, [_P, _P, _I, _D, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_I), _I,
+                             ctypes.POINTER(_I)]),
+    "mx_kernel_name": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libmx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmx.so not found at {LIB_PATH}: run __graft_entry__.build() "
+                              "(the CUDA library is required; there is no CPU path)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != MX_OK:
+        raise MxError(status, lib().mx_last_error().decode())
+
+
+def ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------------------
+# Functions with the C names.
+# ----------------------------------------------------------------------------
+
+def mx_create(params):
+    h = ctypes.c_void_p()
+    check(lib().mx_create(ctypes.byref(h), ctypes.byref(params)))
+    return h
+
+
+def mx_destroy(ctx):
+    check(lib().mx_destroy(ctx))
+
+
+def mx_set_ms_map(ctx, ms, stream=None):
+    check(lib().mx_set_ms_map(ctx, ptr(ms), stream_handle(stream)))
+
+
+def mx_set_anis_map(ctx, ku, axis, stream=None):
+    check(lib().mx_set_anis_map(ctx, ptr(ku), ptr(axis), stream_handle(stream)))
+
+
+def mx_set_bias(ctx, h):
+    arr = (_D * 3)(*[float(v) for v in h])
+    check(lib().mx_set_bias(ctx, arr))
+
+
+def mx_build_demag_kernel(ctx, stream=None):
+    check(lib().mx_build_demag_kernel(ctx, stream_handle(stream)))
+
+
+def mx_heff(ctx, m, h, terms=MX_TERM_ALL, stream=None):
+    check(lib().mx_heff(ctx, ptr(m), ptr(h), int(terms), stream_handle(stream)))
+
+
+def mx_llg_rhs(ctx, m, dmdt, stream=None):
+    check(lib().mx_llg_rhs(ctx, ptr(m), ptr(dmdt), stream_handle(stream)))
+
+
+def mx_rk_step(ctx, m, nsteps, dt, method=MX_RK4, stream=None):
+    check(lib().mx_rk_step(ctx, ptr(m), int(nsteps), float(dt), int(method), stream_handle(stream)))
+
+
+def mx_energy(ctx, m, stream=None):
+    out = (_D * 5)()
+    check(lib().mx_energy(ctx, ptr(m), out, stream_handle(stream)))
+    return list(out)
+
+
+def mx_sync(ctx, stream=None):
+    check(lib().mx_sync(ctx, stream_handle(stream)))
+
+
+def mx_padded_dims(ctx):
+    out = (_I * 3)()
+    check(lib().mx_padded_dims(ctx, out))
+    return tuple(out)
+
+
+def mx_demag_tensor_real(ctx, out, stream=None):
+    check(lib().mx_demag_tensor_real(ctx, ptr(out), stream_handle(stream)))
+
+
+def mx_demag_spectrum(ctx, out, stream=None):
+    check(lib().mx_demag_spectrum(ctx, ptr(out), stream_handle(stream)))
+
+
+def mx_profile_step(ctx, m, nsteps, dt, method=MX_RK4, stream=None, max_kernels=32):
+    ms = (_D * max_kernels)()
+    cnt = (_I * max_kernels)()
+    n = _I()
+    check(lib().mx_profile_step(ctx, ptr(m), int(nsteps), float(dt), int(method), stream_handle(stream),
+                                ms, cnt, max_kernels, ctypes.byref(n)))
+    return {lib().mx_kernel_name(q).decode(): (ms[q], cnt[q]) for q in range(n.value) if cnt[q] > 0}

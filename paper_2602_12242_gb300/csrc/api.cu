@@ -1,0 +1,500 @@
+// C ABI of libmx (declared in include/mx.h): context lifetime, argument
+// checks, the stage sequence of one time step, CUDA-graph replay, energies
+// and per-kernel timing.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mx {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+
+static const char* kNames[KID_COUNT] = {"x_fwd", "yz_fused", "y_fwd", "z_mul", "y_inv", "x_inv",
+                                        "local_stage", "normalize", "copy"};
+const char* kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kNames[id] : ""; }
+
+// ---------------------------------------------------------------------------
+// Profiler: an event pair per launch, harvested when the pool runs out.
+// ---------------------------------------------------------------------------
+struct Profiler {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ids;
+  int used = 0;
+  double ms[KID_COUNT] = {0};
+  int count[KID_COUNT] = {0};
+  cudaError_t err = cudaSuccess;
+  cudaStream_t last = nullptr;
+  void harvest() {
+    if (used == 0) return;
+    cudaError_t e = cudaEventSynchronize(ev[2 * used - 1]);
+    if (e != cudaSuccess) err = e;
+    for (int q = 0; q < used; ++q) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]) == cudaSuccess) {
+        ms[ids[q]] += t;
+        count[ids[q]] += 1;
+      }
+    }
+    used = 0;
+  }
+};
+
+ProfScope::ProfScope(mx_ctx* c, int i, cudaStream_t s) : ctx(c), id(i), st(s) {
+  Profiler* p = ctx->prof;
+  if (!p) return;
+  if (2 * (p->used + 1) > (int)p->ev.size()) p->harvest();
+  p->ids[p->used] = id;
+  cudaEventRecord(p->ev[2 * p->used], st);
+}
+ProfScope::~ProfScope() {
+  Profiler* p = ctx->prof;
+  if (!p) return;
+  cudaEventRecord(p->ev[2 * p->used + 1], st);
+  p->used += 1;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int pad_len(int n) {
+  if (n <= 1) return 1;
+  int p = 1;
+  while (p < 2 * n - 1) p <<= 1;
+  return p;
+}
+
+static mx_status check_vec_ptr(const void* p, const char* what) {
+  if (!p) {
+    set_error(std::string(what) + " is NULL");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (((uintptr_t)p) & 15) {
+    set_error(std::string(what) + " is not 16-byte aligned");
+    return MX_ERR_INVALID_ARG;
+  }
+  return MX_OK;
+}
+
+static mx_status check_ctx(const mx_ctx* ctx) {
+  if (!ctx) {
+    set_error("context is NULL");
+    return MX_ERR_INVALID_ARG;
+  }
+  return MX_OK;
+}
+
+static void invalidate_graph(mx_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  ctx->graph_m = nullptr;
+  ctx->graph_method = -1;
+}
+
+static std::vector<float2> twiddles32(int L) {
+  std::vector<float2> t(L);
+  for (int q = 0; q < L; ++q) {
+    const double a = -2.0 * kPi * q / L;
+    t[q] = make_float2((float)cos(a), (float)sin(a));
+  }
+  return t;
+}
+
+// One time step on stream st.  m is the caller's field (step start, updated
+// in place).
+static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cudaStream_t st) {
+  const bool demag = ctx->p.demag != 0;
+  float4* hd = demag ? ctx->hd : nullptr;
+  if (method == MX_EULER) {
+    if (demag) MX_TRY(demag_field(ctx, m, hd, st));
+    StageIO io{m, hd, m, ctx->acc, ctx->sa, (float)dt, MX_TERM_ALL};
+    MX_TRY(local_stage(ctx, LM_EULER, io, st));
+    return copy_field(ctx, m, ctx->sa, st);
+  }
+  // RK4: m -> sa -> sb -> sa -> m
+  const float4* in[4] = {m, ctx->sa, ctx->sb, ctx->sa};
+  float4* out[4] = {ctx->sa, ctx->sb, ctx->sa, m};
+  const int modes[4] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3};
+  for (int s = 0; s < 4; ++s) {
+    if (demag) MX_TRY(demag_field(ctx, in[s], hd, st));
+    StageIO io{in[s], hd, m, ctx->acc, out[s], (float)dt, MX_TERM_ALL};
+    MX_TRY(local_stage(ctx, modes[s], io, st));
+  }
+  return MX_OK;
+}
+
+}  // namespace mx
+
+using namespace mx;
+
+extern "C" {
+
+const char* mx_last_error(void) { return g_err.c_str(); }
+const char* mx_version(void) { return "libmx 0.1 (sm_103a)"; }
+const char* mx_kernel_name(int q) { return kernel_name(q); }
+
+mx_status mx_create(mx_ctx** out, const mx_params* p) {
+  clear_error();
+  if (!out || !p) {
+    set_error("mx_create: NULL argument");
+    return MX_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 2048 || p->ny > 2048 || p->nz > 2048) {
+    set_error("mx_create: grid must be 1..2048 cells per axis");
+    return MX_ERR_UNSUPPORTED;
+  }
+  if (!(p->dx > 0 && p->dy > 0 && p->dz > 0) || !(p->Ms > 0) || !(p->A >= 0) || !(p->alpha >= 0) ||
+      !(p->gamma > 0) || !(p->Ku == p->Ku) || !(p->D == p->D)) {
+    set_error("mx_create: need dx, dy, dz, Ms, gamma > 0 and A, alpha >= 0");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (p->dmi_interfacial && p->D != 0.0 && !(p->A > 0)) {
+    set_error("mx_create: DMI boundary condition needs A > 0");
+    return MX_ERR_INVALID_ARG;
+  }
+  mx_ctx* ctx = new mx_ctx();
+  ctx->p = *p;
+  cudaGetDevice(&ctx->device);
+  Grid& g = ctx->g;
+  g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+  g.Px = pad_len(p->nx); g.Py = pad_len(p->ny); g.Pz = pad_len(p->nz);
+  if (g.Px > kMaxPad || g.Py > kMaxPad || g.Pz > kMaxPad || !is_pow2(g.Px) || !is_pow2(g.Py) || !is_pow2(g.Pz)) {
+    delete ctx;
+    set_error("mx_create: padded grid exceeds 4096 per axis");
+    return MX_ERR_UNSUPPORTED;
+  }
+  g.Hx = g.Px > 1 ? g.Px / 2 + 1 : 1;
+  g.Oy = g.Py / 2 + 1;
+  g.Oz = g.Pz / 2 + 1;
+  g.ncell = (long)g.nx * g.ny * g.nz;
+  const long nc = g.ncell;
+  bool ok = true;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (ok && cudaMalloc(ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  };
+  const long no = (long)g.Hx * g.Oy * g.Oz;
+  alloc((void**)&ctx->nhat, sizeof(float) * 6 * no);
+  alloc((void**)&ctx->w1, sizeof(float2) * 3 * (long)g.nz * g.ny * g.Hx);
+  alloc((void**)&ctx->tw_x, sizeof(float2) * g.Px);
+  alloc((void**)&ctx->tw_y, sizeof(float2) * g.Py);
+  alloc((void**)&ctx->tw_z, sizeof(float2) * g.Pz);
+  alloc((void**)&ctx->hd, sizeof(float4) * nc);
+  alloc((void**)&ctx->sa, sizeof(float4) * nc);
+  alloc((void**)&ctx->sb, sizeof(float4) * nc);
+  alloc((void**)&ctx->acc, sizeof(float4) * nc);
+  alloc((void**)&ctx->flag, sizeof(int));
+  alloc((void**)&ctx->ered, sizeof(double) * 5);
+  mx_status st = MX_OK;
+  if (ok) st = demag_setup(ctx);
+  if (ok && st == MX_OK && !ctx->fused_yz) alloc((void**)&ctx->w2, sizeof(float2) * 3 * (long)g.nz * g.Py * g.Hx);
+  if (!ok) {
+    mx_destroy(ctx);
+    set_error("mx_create: device allocation failed");
+    return MX_ERR_OOM;
+  }
+  if (st != MX_OK) {
+    mx_destroy(ctx);
+    return st;
+  }
+  std::vector<float2> tx = twiddles32(g.Px), ty = twiddles32(g.Py), tz = twiddles32(g.Pz);
+  if (cudaMemcpy(ctx->tw_x, tx.data(), sizeof(float2) * g.Px, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->tw_y, ty.data(), sizeof(float2) * g.Py, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->tw_z, tz.data(), sizeof(float2) * g.Pz, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(ctx->flag, 0, sizeof(int)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error(std::string("mx_create: ") + cudaGetErrorString(cudaGetLastError()));
+    mx_destroy(ctx);
+    return MX_ERR_CUDA;
+  }
+  *out = ctx;
+  return MX_OK;
+}
+
+mx_status mx_destroy(mx_ctx* ctx) {
+  if (!ctx) return MX_OK;
+  invalidate_graph(ctx);
+  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_y,
+                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+  return MX_OK;
+}
+
+mx_status mx_padded_dims(const mx_ctx* ctx, int out[3]) {
+  MX_TRY(check_ctx(ctx));
+  if (!out) {
+    set_error("mx_padded_dims: NULL out");
+    return MX_ERR_INVALID_ARG;
+  }
+  out[0] = ctx->g.Px;
+  out[1] = ctx->g.Py;
+  out[2] = ctx->g.Pz;
+  return MX_OK;
+}
+
+mx_status mx_set_ms_map(mx_ctx* ctx, const float* ms_dev, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  invalidate_graph(ctx);
+  if (!ms_dev) {
+    if (ctx->ms_map) cudaFree(ctx->ms_map);
+    ctx->ms_map = nullptr;
+    return MX_OK;
+  }
+  if (!ctx->ms_map && cudaMalloc(&ctx->ms_map, sizeof(float) * ctx->g.ncell) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ms_map = nullptr;
+    set_error("mx_set_ms_map: allocation failed");
+    return MX_ERR_OOM;
+  }
+  MX_CUDA_TRY(cudaMemcpyAsync(ctx->ms_map, ms_dev, sizeof(float) * ctx->g.ncell, cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+  return MX_OK;
+}
+
+mx_status mx_set_anis_map(mx_ctx* ctx, const float* ku_dev, const float* axis_dev, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  invalidate_graph(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  const long nc = ctx->g.ncell;
+  if (ku_dev) {
+    if (!ctx->ku_map && cudaMalloc(&ctx->ku_map, sizeof(float) * nc) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->ku_map = nullptr;
+      set_error("mx_set_anis_map: allocation failed");
+      return MX_ERR_OOM;
+    }
+    MX_CUDA_TRY(cudaMemcpyAsync(ctx->ku_map, ku_dev, sizeof(float) * nc, cudaMemcpyDeviceToDevice, st));
+  } else if (ctx->ku_map) {
+    cudaFree(ctx->ku_map);
+    ctx->ku_map = nullptr;
+  }
+  if (axis_dev) {
+    MX_TRY(check_vec_ptr(axis_dev, "mx_set_anis_map: axis"));
+    if (!ctx->axis_map && cudaMalloc(&ctx->axis_map, sizeof(float4) * nc) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->axis_map = nullptr;
+      set_error("mx_set_anis_map: allocation failed");
+      return MX_ERR_OOM;
+    }
+    MX_CUDA_TRY(cudaMemcpyAsync(ctx->axis_map, axis_dev, sizeof(float4) * nc, cudaMemcpyDeviceToDevice, st));
+  } else if (ctx->axis_map) {
+    cudaFree(ctx->axis_map);
+    ctx->axis_map = nullptr;
+  }
+  return MX_OK;
+}
+
+mx_status mx_set_bias(mx_ctx* ctx, const double h[3]) {
+  MX_TRY(check_ctx(ctx));
+  if (!h) {
+    set_error("mx_set_bias: NULL h");
+    return MX_ERR_INVALID_ARG;
+  }
+  invalidate_graph(ctx);
+  for (int q = 0; q < 3; ++q) ctx->p.h_bias[q] = h[q];
+  return MX_OK;
+}
+
+mx_status mx_build_demag_kernel(mx_ctx* ctx, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  invalidate_graph(ctx);
+  return build_demag_kernel(ctx, (cudaStream_t)stream);
+}
+
+mx_status mx_heff(mx_ctx* ctx, const float* m, float* h, int terms, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(m, "mx_heff: m"));
+  MX_TRY(check_vec_ptr(h, "mx_heff: h"));
+  if (m == h || (terms & ~MX_TERM_ALL)) {
+    set_error("mx_heff: m and h overlap or bad term mask");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool demag = (terms & MX_TERM_DEMAG) != 0;
+  if (demag && !ctx->built) {
+    set_error("mx_heff: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  if (demag) MX_TRY(demag_field(ctx, (const float4*)m, ctx->hd, st));
+  StageIO io{(const float4*)m, demag ? ctx->hd : nullptr, nullptr, nullptr, (float4*)h, 0.f, terms};
+  return local_stage(ctx, LM_HEFF, io, st);
+}
+
+mx_status mx_llg_rhs(mx_ctx* ctx, const float* m, float* dmdt, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(m, "mx_llg_rhs: m"));
+  MX_TRY(check_vec_ptr(dmdt, "mx_llg_rhs: dmdt"));
+  if (m == dmdt) {
+    set_error("mx_llg_rhs: m and dmdt overlap");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool demag = ctx->p.demag != 0;
+  if (demag && !ctx->built) {
+    set_error("mx_llg_rhs: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  if (demag) MX_TRY(demag_field(ctx, (const float4*)m, ctx->hd, st));
+  StageIO io{(const float4*)m, demag ? ctx->hd : nullptr, nullptr, nullptr, (float4*)dmdt, 0.f, MX_TERM_ALL};
+  return local_stage(ctx, LM_RHS, io, st);
+}
+
+static mx_status check_step_args(mx_ctx* ctx, const float* m, int nsteps, double dt, int method) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(m, "mx_rk_step: m"));
+  if (nsteps < 0 || !(dt > 0) || !isfinite(dt) || (method != MX_RK4 && method != MX_EULER)) {
+    set_error("mx_rk_step: need nsteps >= 0, finite dt > 0, method MX_RK4 or MX_EULER");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (ctx->p.demag && !ctx->built) {
+    set_error("mx_rk_step: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  return MX_OK;
+}
+
+mx_status mx_rk_step(mx_ctx* ctx, float* m, int nsteps, double dt, int method, mx_stream_t stream) {
+  MX_TRY(check_step_args(ctx, m, nsteps, dt, method));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nsteps == 0) return MX_OK;
+  MX_TRY(normalize_field(ctx, (float4*)m, st));
+  if (!ctx->graph || ctx->graph_m != m || ctx->graph_dt != dt || ctx->graph_method != method) {
+    invalidate_graph(ctx);
+    cudaGraph_t graph = nullptr;
+    MX_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    mx_status s = enqueue_step(ctx, (float4*)m, dt, method, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (s != MX_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) {
+      set_error(std::string("mx_rk_step: capture failed: ") + cudaGetErrorString(e));
+      return MX_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      ctx->graph = nullptr;
+      set_error(std::string("mx_rk_step: instantiate failed: ") + cudaGetErrorString(e));
+      return MX_ERR_CUDA;
+    }
+    ctx->graph_m = m;
+    ctx->graph_dt = dt;
+    ctx->graph_method = method;
+  }
+  for (int s = 0; s < nsteps; ++s) MX_CUDA_TRY(cudaGraphLaunch(ctx->graph, st));
+  return MX_OK;
+}
+
+mx_status mx_profile_step(mx_ctx* ctx, float* m, int nsteps, double dt, int method, mx_stream_t stream,
+                          double* ms_total, int* launches, int max_kernels, int* n_kernels) {
+  MX_TRY(check_step_args(ctx, m, nsteps, dt, method));
+  if (!ms_total || !launches || !n_kernels || max_kernels < 1) {
+    set_error("mx_profile_step: NULL output");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Profiler prof;
+  const int pool = 4096;
+  prof.ev.resize(2 * pool);
+  prof.ids.resize(pool);
+  for (auto& e : prof.ev) MX_CUDA_TRY(cudaEventCreate(&e));
+  ctx->prof = &prof;
+  mx_status s = normalize_field(ctx, (float4*)m, st);
+  for (int q = 0; q < nsteps && s == MX_OK; ++q) s = enqueue_step(ctx, (float4*)m, dt, method, st);
+  prof.harvest();
+  ctx->prof = nullptr;
+  for (auto& e : prof.ev) cudaEventDestroy(e);
+  if (s != MX_OK) return s;
+  if (prof.err != cudaSuccess) {
+    set_error(std::string("mx_profile_step: ") + cudaGetErrorString(prof.err));
+    return MX_ERR_CUDA;
+  }
+  const int n = KID_COUNT < max_kernels ? KID_COUNT : max_kernels;
+  for (int q = 0; q < n; ++q) {
+    ms_total[q] = prof.ms[q];
+    launches[q] = prof.count[q];
+  }
+  *n_kernels = n;
+  return MX_OK;
+}
+
+mx_status mx_energy(mx_ctx* ctx, const float* m, double e_out[5], mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(m, "mx_energy: m"));
+  if (!e_out) {
+    set_error("mx_energy: NULL e_out");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool demag = ctx->p.demag != 0;
+  if (demag && !ctx->built) {
+    set_error("mx_energy: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  if (demag) MX_TRY(demag_field(ctx, (const float4*)m, ctx->hd, st));
+  MX_CUDA_TRY(cudaMemsetAsync(ctx->ered, 0, sizeof(double) * 5, st));
+  MX_TRY(energy_terms(ctx, (const float4*)m, demag ? ctx->hd : nullptr, ctx->ered, st));
+  MX_CUDA_TRY(cudaMemcpyAsync(e_out, ctx->ered, sizeof(double) * 5, cudaMemcpyDeviceToHost, st));
+  MX_CUDA_TRY(cudaStreamSynchronize(st));
+  return MX_OK;
+}
+
+mx_status mx_sync(mx_ctx* ctx, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  cudaStream_t st = (cudaStream_t)stream;
+  int flag = 0;
+  MX_CUDA_TRY(cudaMemcpyAsync(&flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MX_CUDA_TRY(cudaStreamSynchronize(st));
+  if (flag) {
+    MX_CUDA_TRY(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st));
+    MX_CUDA_TRY(cudaStreamSynchronize(st));
+    set_error("mx_sync: a kernel produced a non-finite value");
+    return MX_ERR_NONFINITE;
+  }
+  return MX_OK;
+}
+
+mx_status mx_demag_tensor_real(mx_ctx* ctx, double* out, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  if (!out) {
+    set_error("mx_demag_tensor_real: NULL out");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (!ctx->built || !ctx->t_real) {
+    set_error("mx_demag_tensor_real: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  MX_CUDA_TRY(cudaMemcpyAsync(out, ctx->t_real, sizeof(double) * 6 * ctx->g.ncell, cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+  return MX_OK;
+}
+
+mx_status mx_demag_spectrum(mx_ctx* ctx, float* out, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  if (!out) {
+    set_error("mx_demag_spectrum: NULL out");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (!ctx->built) {
+    set_error("mx_demag_spectrum: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  const long no = (long)ctx->g.Hx * ctx->g.Oy * ctx->g.Oz;
+  MX_CUDA_TRY(cudaMemcpyAsync(out, ctx->nhat, sizeof(float) * 6 * no, cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+  return MX_OK;
+}
+
+}  // extern "C"

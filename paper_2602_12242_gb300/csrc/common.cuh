@@ -1,0 +1,143 @@
+// Shared definitions of libmx: context layout, error reporting, complex helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/mx.h"
+
+namespace mx {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4e-7 * kPi;  // vacuum permeability [T m/A]
+constexpr int kMaxPad = 4096;         // largest padded length per axis
+
+// ---------------------------------------------------------------------------
+// Error reporting: a per-thread message plus a status code.
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+void clear_error();
+
+#define MX_CUDA_TRY(expr)                                                         \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ::mx::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));        \
+      return MX_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+
+#define MX_TRY(expr)                       \
+  do {                                     \
+    mx_status s_ = (expr);                 \
+    if (s_ != MX_OK) return s_;            \
+  } while (0)
+
+// Check the launch that was just enqueued.
+inline mx_status launch_check(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return MX_ERR_CUDA;
+  }
+  return MX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Complex arithmetic on float2 / double2.
+// ---------------------------------------------------------------------------
+template <typename C> struct real_of;
+template <> struct real_of<float2> { typedef float type; };
+template <> struct real_of<double2> { typedef double type; };
+
+template <typename C> __host__ __device__ __forceinline__ C mkc(typename real_of<C>::type r, typename real_of<C>::type i) {
+  C c; c.x = r; c.y = i; return c;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mkc<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mkc<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mkc<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mkc<C>(a.x, -a.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, typename real_of<C>::type s) { return mkc<C>(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C cmul_mi(C a) {
+  return INV ? mkc<C>(-a.y, a.x) : mkc<C>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Derived per-context constants passed to kernels by value.
+// ---------------------------------------------------------------------------
+struct Grid {
+  int nx, ny, nz;      // cells
+  int Px, Py, Pz;      // padded lengths
+  int Hx;              // Px/2 + 1 (half spectrum along x); 1 when Px == 1
+  int Oy, Oz;          // Py/2 + 1, Pz/2 + 1 (octant extents of the spectrum)
+  long ncell;
+};
+
+struct LocalCoef {
+  float inv_dx2, inv_dy2, inv_dz2;   // 1/h^2
+  float inv_2dx, inv_2dy;            // 1/(2h) for central differences
+  float kdx, kdy;                    // h * D/(2A): chiral ghost strength
+  float cA;                          // 2A/mu0      (divide by Ms_i)
+  float cD;                          // 2D/mu0      (divide by Ms_i)
+  float cK;                          // 2Ku/mu0     (scalar Ku; divide by Ms_i)
+  float Ms;                          // scalar Ms
+  float ax, ay, az;                  // scalar easy axis (unit)
+  float hx, hy, hz;                  // bias
+  float llg;                         // -gamma0/(1+alpha^2)
+  float alpha;
+  int dmi, precession;
+  const float* ms_map;               // may be null
+  const float* ku_map;               // may be null (then cK)
+  const float4* axis_map;            // may be null (then ax, ay, az)
+};
+
+struct Profiler;
+
+}  // namespace mx
+
+// The context (opaque to callers).
+struct mx_ctx {
+  mx_params p;
+  int device;
+  mx::Grid g;
+
+  // material maps (context copies)
+  float* ms_map = nullptr;
+  float* ku_map = nullptr;
+  float4* axis_map = nullptr;
+
+  // demag
+  bool built = false;
+  float* nhat = nullptr;          // 6 x Oz x Oy x Hx
+  float2* w1 = nullptr;           // 3 x nz x ny x Hx   (after the x pass)
+  float2* w2 = nullptr;           // 3 x nz x Py x Hx   (after the y pass; unfused path)
+  float2* tw_x = nullptr;         // W_Px^k, k < Px
+  float2* tw_y = nullptr;         // W_Py^k, k < Py
+  float2* tw_z = nullptr;         // W_Pz^k, k < Pz
+  bool fused_yz = false;          // y/z passes in one kernel (plane fits on chip)
+  int yz_tile = 1;                // kx columns per block in the fused kernel
+  double* t_real = nullptr;       // FP64 real-space tensor octant (kept for checking)
+  double spectrum_imag_ratio = 0; // max|Im| / max|Re| of the FP64 tensor spectrum
+
+  // stage buffers
+  float4* hd = nullptr;           // demag field
+  float4* sa = nullptr;           // stage input A
+  float4* sb = nullptr;           // stage input B
+  float4* acc = nullptr;          // RK accumulator
+  int* flag = nullptr;            // non-finite flag
+  double* ered = nullptr;         // energy accumulators (5)
+
+  // CUDA graph cache for mx_rk_step
+  cudaGraphExec_t graph = nullptr;
+  const float* graph_m = nullptr;
+  double graph_dt = 0.0;
+  int graph_method = -1;
+  cudaStream_t cap_stream = nullptr;
+
+  // profiling hook (events around each launch when non-null)
+  mx::Profiler* prof = nullptr;
+};

@@ -1,0 +1,57 @@
+// Declarations shared by the translation units of libmx.
+#pragma once
+
+#include "common.cuh"
+
+namespace mx {
+
+// Kernel identifiers for mx_profile_step.
+enum KernelId {
+  KID_X_FWD = 0,
+  KID_YZ,
+  KID_Y_FWD,
+  KID_Z_MUL,
+  KID_Y_INV,
+  KID_X_INV,
+  KID_LOCAL,
+  KID_NORMALIZE,
+  KID_COPY,
+  KID_COUNT
+};
+const char* kernel_name(int id);
+
+// Records a CUDA event pair around the launches in its scope when the context
+// is being profiled; does nothing otherwise.
+struct ProfScope {
+  mx_ctx* ctx;
+  int id;
+  cudaStream_t st;
+  ProfScope(mx_ctx* c, int i, cudaStream_t s);
+  ~ProfScope();
+};
+
+// demag.cu
+mx_status demag_setup(mx_ctx* ctx);
+mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st);
+
+// newell.cu
+mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st);
+
+// local.cu
+enum LocalMode { LM_HEFF = 0, LM_RHS, LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3, LM_EULER };
+struct StageIO {
+  const float4* m;    // field the stencil and LLG act on
+  const float4* hd;   // demag field (null: no demag term)
+  const float4* m0;   // step start (RK stages 1..3)
+  float4* acc;        // RK accumulator
+  float4* out;        // H_eff, dm/dt, next stage input or the new m
+  float dt;
+  int terms;          // MX_TERM_* mask (LM_HEFF only)
+};
+LocalCoef local_coef(const mx_ctx* ctx);
+mx_status local_stage(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st);
+mx_status normalize_field(mx_ctx* ctx, float4* m, cudaStream_t st);
+mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t st);
+mx_status energy_terms(mx_ctx* ctx, const float4* m, const float4* hd, double* e_dev, cudaStream_t st);
+
+}  // namespace mx

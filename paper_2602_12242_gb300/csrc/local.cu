@@ -1,0 +1,276 @@
+// Fused local kernel: exchange / DMI / anisotropy / Zeeman fields, the demag
+// field read from the convolution, the LLG right-hand side and the RK stage
+// update with renormalisation, one thread per cell with float4 access.
+//
+//   exchange  H = 2A/(mu0 Ms_i) sum_d (m_{i+d} + m_{i-d} - 2 m_i)/h_d^2
+//             (Sec. II-A exchange term, second-order central differences of
+//             Sec. II-B)
+//   DMI       H = 2D/(mu0 Ms_i) (d_x m_z, d_y m_z, -(d_x m_x + d_y m_y)),
+//             central differences in x and y (Sec. II-A interfacial form)
+//   boundary  a missing neighbour across the face with outward normal n is
+//             the ghost m_b - h (D/2A) (e_z x n) x m_b, the discrete form of
+//             dm/dx_k = -(D/2A)(e_z x e_k) x m (Sec. II-A, II-B); with DMI off
+//             (or on z faces) this is m_b, the Neumann condition
+//   anisotropy H = 2 Ku/(mu0 Ms_i) (m.e) e
+//   LLG       dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)]  (Eq. 1)
+//   RK4       k_s at stage s; acc = k1 + 2k2 + 2k3; stage inputs
+//             normalize(m0 + c dt k), result normalize(m0 + dt/6 (acc + k4))
+//             (renormalisation after every stage, Sec. II-B)
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mx {
+
+struct Terms {
+  float3 demag, exch, dmi, anis, zee;
+};
+
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// All field terms at cell (i, j, k).
+template <bool DMI>
+__device__ __forceinline__ void local_terms(const float4* __restrict__ m, const float4* __restrict__ hd,
+                                            const Grid& g, const LocalCoef& c, int i, int j, int k, long idx,
+                                            float3 mc, float inv_ms, Terms& t) {
+  const long sx = 1, sy = g.nx, sz = (long)g.nx * g.ny;
+  float3 xm, xp, ym, yp, zm, zp;
+  // chiral ghosts (kdx, kdy are zero when DMI is off)
+  xp = (i + 1 < g.nx) ? f3(__ldg(&m[idx + sx])) : make_float3(mc.x - c.kdx * mc.z, mc.y, mc.z + c.kdx * mc.x);
+  xm = (i > 0) ? f3(__ldg(&m[idx - sx])) : make_float3(mc.x + c.kdx * mc.z, mc.y, mc.z - c.kdx * mc.x);
+  yp = (j + 1 < g.ny) ? f3(__ldg(&m[idx + sy])) : make_float3(mc.x, mc.y - c.kdy * mc.z, mc.z + c.kdy * mc.y);
+  ym = (j > 0) ? f3(__ldg(&m[idx - sy])) : make_float3(mc.x, mc.y + c.kdy * mc.z, mc.z - c.kdy * mc.y);
+  zp = (k + 1 < g.nz) ? f3(__ldg(&m[idx + sz])) : mc;
+  zm = (k > 0) ? f3(__ldg(&m[idx - sz])) : mc;
+  const float3 two = 2.f * mc;
+  const float3 lap = c.inv_dx2 * (xp + xm - two) + c.inv_dy2 * (yp + ym - two) + c.inv_dz2 * (zp + zm - two);
+  t.exch = (c.cA * inv_ms) * lap;
+  if (DMI) {
+    const float3 ddx = c.inv_2dx * (xp - xm);
+    const float3 ddy = c.inv_2dy * (yp - ym);
+    t.dmi = (c.cD * inv_ms) * make_float3(ddx.z, ddy.z, -(ddx.x + ddy.y));
+  } else {
+    t.dmi = make_float3(0.f, 0.f, 0.f);
+  }
+  const float3 e = c.axis_map ? f3(__ldg(&c.axis_map[idx])) : make_float3(c.ax, c.ay, c.az);
+  const float cK = c.ku_map ? (__ldg(&c.ku_map[idx]) * (float)(2.0 / kMu0)) : c.cK;
+  t.anis = (cK * inv_ms * dot3(mc, e)) * e;
+  t.zee = make_float3(c.hx, c.hy, c.hz);
+  t.demag = hd ? f3(__ldg(&hd[idx])) : make_float3(0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float3 llg(const LocalCoef& c, float3 mc, float3 H) {
+  const float3 mxH = cross3(mc, H);
+  const float3 mxmxH = cross3(mc, mxH);
+  const float3 p = c.precession ? mxH : make_float3(0.f, 0.f, 0.f);
+  return c.llg * (p + c.alpha * mxmxH);
+}
+
+__device__ __forceinline__ float3 unit(float3 v) {
+  const float r = rnorm3df(v.x, v.y, v.z);
+  return r * v;
+}
+
+template <int MODE, bool DMI>
+__global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoef c, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  const float3 mc = f3(io.m[idx]);
+  const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
+  const float inv_ms = 1.f / ms;
+  Terms t;
+  local_terms<DMI>(io.m, io.hd, g, c, i, j, k, idx, mc, inv_ms, t);
+  float3 out;
+  if (MODE == LM_HEFF) {
+    out = make_float3(0.f, 0.f, 0.f);
+    if (io.terms & MX_TERM_DEMAG) out = out + t.demag;
+    if (io.terms & MX_TERM_EXCH) out = out + t.exch;
+    if (io.terms & MX_TERM_ANIS) out = out + t.anis;
+    if (io.terms & MX_TERM_DMI) out = out + t.dmi;
+    if (io.terms & MX_TERM_ZEEMAN) out = out + t.zee;
+  } else {
+    const float3 H = t.demag + t.exch + t.anis + t.dmi + t.zee;
+    const float3 kk = llg(c, mc, H);
+    if (MODE == LM_RHS) {
+      out = kk;
+    } else if (MODE == LM_EULER) {
+      out = unit(mc + io.dt * kk);
+    } else if (MODE == LM_RK4_S0) {
+      io.acc[idx] = make_float4(kk.x, kk.y, kk.z, 0.f);
+      out = unit(mc + (0.5f * io.dt) * kk);
+    } else {
+      const float3 m0 = f3(io.m0[idx]);
+      const float3 a = f3(io.acc[idx]);
+      if (MODE == LM_RK4_S3) {
+        out = unit(m0 + (io.dt * (1.f / 6.f)) * (a + kk));
+      } else {
+        io.acc[idx] = make_float4(a.x + 2.f * kk.x, a.y + 2.f * kk.y, a.z + 2.f * kk.z, 0.f);
+        out = unit(m0 + ((MODE == LM_RK4_S1 ? 0.5f : 1.f) * io.dt) * kk);
+      }
+    }
+  }
+  if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, 1);
+  io.out[idx] = make_float4(out.x, out.y, out.z, 0.f);
+}
+
+__global__ void normalize_kernel(float4* m, long n, int* flag) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const float4 v = m[idx];
+  const float r = rnorm3df(v.x, v.y, v.z);
+  const float4 o = make_float4(v.x * r, v.y * r, v.z * r, 0.f);
+  if (!(isfinite(o.x) && isfinite(o.y) && isfinite(o.z))) atomicOr(flag, 1);
+  m[idx] = o;
+}
+
+__global__ void copy_kernel(float4* __restrict__ dst, const float4* __restrict__ src, long n) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n) dst[idx] = src[idx];
+}
+
+// Energies: [demag, exch, anis, dmi, zeeman], FP64 block sums then atomics.
+template <bool DMI>
+__global__ void __launch_bounds__(256) energy_kernel(const float4* __restrict__ m, const float4* __restrict__ hd,
+                                                     Grid g, LocalCoef c, double V, double Ku, double* e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double acc[5] = {0, 0, 0, 0, 0};
+  if (i < g.nx && j < g.ny) {
+    const long idx = ((long)k * g.ny + j) * g.nx + i;
+    const float3 mc = f3(m[idx]);
+    const float ms = c.ms_map ? c.ms_map[idx] : c.Ms;
+    Terms t;
+    local_terms<DMI>(m, hd, g, c, i, j, k, idx, mc, 1.f / ms, t);
+    const double q = -0.5 * kMu0 * V * (double)ms;
+    acc[0] = q * (double)dot3(mc, t.demag);
+    acc[1] = q * (double)dot3(mc, t.exch);
+    const float3 e3 = c.axis_map ? f3(c.axis_map[idx]) : make_float3(c.ax, c.ay, c.az);
+    const double ku = c.ku_map ? (double)c.ku_map[idx] : Ku;
+    const double me = (double)dot3(mc, e3);
+    acc[2] = V * ku * (1.0 - me * me);
+    acc[3] = q * (double)dot3(mc, t.dmi);
+    acc[4] = 2.0 * q * (double)dot3(mc, t.zee);
+  }
+  __shared__ double red[5][8];
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int q = 0; q < 5; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (tid < 5) {
+    double s = 0.0;
+    const int nw = (blockDim.x * blockDim.y + 31) / 32;
+    for (int w = 0; w < nw; ++w) s += red[tid][w];
+    atomicAdd(&e[tid], s);
+  }
+}
+
+LocalCoef local_coef(const mx_ctx* ctx) {
+  const mx_params& p = ctx->p;
+  LocalCoef c;
+  c.inv_dx2 = (float)(1.0 / (p.dx * p.dx));
+  c.inv_dy2 = (float)(1.0 / (p.dy * p.dy));
+  c.inv_dz2 = (float)(1.0 / (p.dz * p.dz));
+  c.inv_2dx = (float)(0.5 / p.dx);
+  c.inv_2dy = (float)(0.5 / p.dy);
+  const bool dmi = p.dmi_interfacial && p.D != 0.0 && p.A > 0.0;
+  const double kappa = dmi ? p.D / (2.0 * p.A) : 0.0;
+  c.kdx = (float)(p.dx * kappa);
+  c.kdy = (float)(p.dy * kappa);
+  c.cA = (float)(2.0 * p.A / kMu0);
+  c.cD = (float)(2.0 * p.D / kMu0);
+  c.cK = (float)(2.0 * p.Ku / kMu0);
+  c.Ms = (float)p.Ms;
+  double ax = p.ku_axis[0], ay = p.ku_axis[1], az = p.ku_axis[2];
+  double an = sqrt(ax * ax + ay * ay + az * az);
+  if (an > 0) { ax /= an; ay /= an; az /= an; }
+  c.ax = (float)ax; c.ay = (float)ay; c.az = (float)az;
+  c.hx = (float)p.h_bias[0];
+  c.hy = (float)p.h_bias[1];
+  c.hz = (float)p.h_bias[2];
+  c.llg = (float)(-p.gamma / (1.0 + p.alpha * p.alpha));
+  c.alpha = (float)p.alpha;
+  c.dmi = dmi ? 1 : 0;
+  c.precession = p.precession ? 1 : 0;
+  c.ms_map = ctx->ms_map;
+  c.ku_map = ctx->ku_map;
+  c.axis_map = ctx->axis_map;
+  return c;
+}
+
+template <int MODE>
+static void launch_local(bool dmi, dim3 grid, dim3 block, cudaStream_t st, const StageIO& io, const Grid& g,
+                         const LocalCoef& c, int* flag) {
+  if (dmi)
+    local_kernel<MODE, true><<<grid, block, 0, st>>>(io, g, c, flag);
+  else
+    local_kernel<MODE, false><<<grid, block, 0, st>>>(io, g, c, flag);
+}
+
+static void local_dims(const Grid& g, dim3& grid, dim3& block) {
+  block = dim3(32, 8, 1);
+  if (g.nx < 32) block = dim3(g.nx <= 8 ? 8 : (g.nx <= 16 ? 16 : 32), 256 / (g.nx <= 8 ? 8 : (g.nx <= 16 ? 16 : 32)), 1);
+  grid = dim3((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+}
+
+mx_status local_stage(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st) {
+  const Grid& g = ctx->g;
+  const LocalCoef c = local_coef(ctx);
+  dim3 grid, block;
+  local_dims(g, grid, block);
+  const bool dmi = c.dmi != 0;
+  ProfScope ps(ctx, KID_LOCAL, st);
+  switch (mode) {
+    case LM_HEFF: launch_local<LM_HEFF>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    case LM_RHS: launch_local<LM_RHS>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    case LM_RK4_S0: launch_local<LM_RK4_S0>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    case LM_RK4_S1: launch_local<LM_RK4_S1>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    case LM_RK4_S2: launch_local<LM_RK4_S2>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    case LM_RK4_S3: launch_local<LM_RK4_S3>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    case LM_EULER: launch_local<LM_EULER>(dmi, grid, block, st, io, g, c, ctx->flag); break;
+    default: set_error("local_stage: bad mode"); return MX_ERR_INVALID_ARG;
+  }
+  return launch_check("local_kernel");
+}
+
+mx_status normalize_field(mx_ctx* ctx, float4* m, cudaStream_t st) {
+  const long n = ctx->g.ncell;
+  ProfScope ps(ctx, KID_NORMALIZE, st);
+  normalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m, n, ctx->flag);
+  return launch_check("normalize_kernel");
+}
+
+mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t st) {
+  const long n = ctx->g.ncell;
+  ProfScope ps(ctx, KID_COPY, st);
+  copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, src, n);
+  return launch_check("copy_kernel");
+}
+
+mx_status energy_terms(mx_ctx* ctx, const float4* m, const float4* hd, double* e_dev, cudaStream_t st) {
+  const Grid& g = ctx->g;
+  const LocalCoef c = local_coef(ctx);
+  dim3 grid, block;
+  local_dims(g, grid, block);
+  const double V = ctx->p.dx * ctx->p.dy * ctx->p.dz;
+  if (c.dmi)
+    energy_kernel<true><<<grid, block, 0, st>>>(m, hd, g, c, V, ctx->p.Ku, e_dev);
+  else
+    energy_kernel<false><<<grid, block, 0, st>>>(m, hd, g, c, V, ctx->p.Ku, e_dev);
+  return launch_check("energy_kernel");
+}
+
+}  // namespace mx

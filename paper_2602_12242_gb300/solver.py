@@ -1,0 +1,154 @@
+"""Context object over the C ABI (argument marshalling only).
+
+``Context`` owns one ``mx_ctx`` and exposes the entry points of include/mx.h
+as methods on torch CUDA tensors.  No arithmetic of the method happens here.
+"""
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def to_dev4(a, device="cuda"):
+    """(nz, ny, nx, 3) array -> contiguous float32 CUDA tensor (nz, ny, nx, 4)."""
+    a = torch.as_tensor(np.asarray(a, dtype=np.float32))
+    out = torch.zeros(a.shape[:-1] + (4,), dtype=torch.float32)
+    out[..., :3] = a
+    return out.to(device).contiguous()
+
+
+def from_dev4(t):
+    """(nz, ny, nx, 4) CUDA tensor -> (nz, ny, nx, 3) float64 numpy array."""
+    return t[..., :3].double().cpu().numpy()
+
+
+class Context:
+    """One simulation grid: parameters, demag kernel and workspaces on one GPU."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, Ms=8e5, A=1.3e-11, Ku=0.0, D=0.0, alpha=0.5,
+                 gamma=2.211e5, ku_axis=(0.0, 0.0, 1.0), h_bias=(0.0, 0.0, 0.0), dmi=False,
+                 precession=True, demag=True, build=True, stream=None):
+        p = L.mx_params()
+        p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+        p.dx, p.dy, p.dz = float(dx), float(dy), float(dz)
+        p.Ms, p.A, p.Ku, p.D = float(Ms), float(A), float(Ku), float(D)
+        p.alpha, p.gamma = float(alpha), float(gamma)
+        p.ku_axis[:] = [float(v) for v in ku_axis]
+        p.h_bias[:] = [float(v) for v in h_bias]
+        p.dmi_interfacial, p.precession, p.demag = int(bool(dmi)), int(bool(precession)), int(bool(demag))
+        self.params = p
+        self.shape = (int(nz), int(ny), int(nx))
+        self.h = None
+        self.h = L.mx_create(p)
+        if build and demag:
+            self.build_demag_kernel(stream)
+
+    @classmethod
+    def from_config(cls, cfg, Ms=None, Ku=None, ku_axis=None, **kw):
+        c = dict(cfg)
+        ms = c["Ms"] if Ms is None else Ms
+        axis = c["ku_axis"] if ku_axis is None else ku_axis
+        ms_scalar = float(ms) if np.isscalar(ms) else float(np.mean(ms))
+        axis_scalar = axis if (not isinstance(axis, np.ndarray) or axis.ndim == 1) else (0.0, 0.0, 1.0)
+        ku = c["Ku"] if Ku is None else Ku
+        ku_scalar = float(ku) if np.isscalar(ku) else 0.0
+        ctx = cls(c["nx"], c["ny"], c["nz"], c["dx"], c["dy"], c["dz"], Ms=ms_scalar, A=c["A"], Ku=ku_scalar,
+                  D=c["D"], alpha=c["alpha"], gamma=c["gamma"], ku_axis=axis_scalar, h_bias=c["h_bias"],
+                  dmi=c["dmi"], build=False, **kw)
+        if not np.isscalar(ms):
+            ctx.set_ms_map(torch.as_tensor(np.asarray(ms, np.float32)).cuda())
+        ku_map = None if np.isscalar(ku) else torch.as_tensor(np.asarray(ku, np.float32)).cuda()
+        ax_map = None
+        if isinstance(axis, np.ndarray) and axis.ndim > 1:
+            ax_map = to_dev4(axis)
+        if ku_map is not None or ax_map is not None:
+            if ku_map is None and ku_scalar != 0.0:
+                ku_map = torch.full(ctx.shape, ku_scalar, dtype=torch.float32, device="cuda")
+            ctx.set_anis_map(ku_map, ax_map)
+        if ctx.params.demag:
+            ctx.build_demag_kernel()
+        return ctx
+
+    def close(self):
+        if self.h is not None:
+            L.mx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup ---------------------------------------------------------------
+    def build_demag_kernel(self, stream=None):
+        L.mx_build_demag_kernel(self.h, stream)
+
+    def set_ms_map(self, ms, stream=None):
+        L.mx_set_ms_map(self.h, None if ms is None else ms.contiguous(), stream)
+        if stream is None:
+            torch.cuda.current_stream().synchronize()
+
+    def set_anis_map(self, ku, axis, stream=None):
+        L.mx_set_anis_map(self.h, None if ku is None else ku.contiguous(),
+                          None if axis is None else axis.contiguous(), stream)
+        if stream is None:
+            torch.cuda.current_stream().synchronize()
+
+    def set_bias(self, h):
+        L.mx_set_bias(self.h, h)
+
+    @property
+    def padded_dims(self):
+        return L.mx_padded_dims(self.h)
+
+    # -- hot path ------------------------------------------------------------
+    def _check(self, t):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != self.shape + (4,):
+            raise ValueError(f"expected contiguous CUDA float32 tensor of shape {self.shape + (4,)}")
+
+    def heff(self, m, out=None, terms=L.MX_TERM_ALL, stream=None):
+        self._check(m)
+        out = torch.empty_like(m) if out is None else out
+        self._check(out)
+        L.mx_heff(self.h, m, out, terms, stream)
+        return out
+
+    def llg_rhs(self, m, out=None, stream=None):
+        self._check(m)
+        out = torch.empty_like(m) if out is None else out
+        self._check(out)
+        L.mx_llg_rhs(self.h, m, out, stream)
+        return out
+
+    def rk_step(self, m, nsteps, dt, method="rk4", stream=None):
+        self._check(m)
+        L.mx_rk_step(self.h, m, nsteps, dt, L.MX_RK4 if method == "rk4" else L.MX_EULER, stream)
+        return m
+
+    def energy(self, m, stream=None):
+        self._check(m)
+        e = L.mx_energy(self.h, m, stream)
+        return dict(zip(("demag", "exch", "anis", "dmi", "zeeman"), e))
+
+    def sync(self, stream=None):
+        L.mx_sync(self.h, stream)
+
+    def demag_tensor_real(self):
+        nz, ny, nx = self.shape
+        out = torch.empty((6, nz, ny, nx), dtype=torch.float64, device="cuda")
+        L.mx_demag_tensor_real(self.h, out)
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def demag_spectrum(self):
+        Px, Py, Pz = self.padded_dims
+        Hx = Px // 2 + 1 if Px > 1 else 1
+        out = torch.empty((6, Pz // 2 + 1, Py // 2 + 1, Hx), dtype=torch.float32, device="cuda")
+        L.mx_demag_spectrum(self.h, out)
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def profile_step(self, m, nsteps, dt, method="rk4", stream=None):
+        self._check(m)
+        return L.mx_profile_step(self.h, m, nsteps, dt, L.MX_RK4 if method == "rk4" else L.MX_EULER, stream)
