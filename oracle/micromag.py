@@ -34,8 +34,10 @@ Paper passages followed (MagneX, Sec. II):
 """
 from dataclasses import dataclass, field
 import math
+import os
 
 import numpy as np
+import scipy.fft as sfft
 import torch
 
 from . import tensor as _tensor
@@ -93,8 +95,12 @@ def normalize(m):
 # Demagnetisation
 # --------------------------------------------------------------------------
 
+def _workers():
+    return os.cpu_count() or 1
+
+
 def padded_tensor_spectrum(p):
-    """rfftn of the tensor placed on the 2n-padded grid, shape (6, Pz, Py, Px//2+1)."""
+    """rfftn of the tensor placed on the 2n-padded grid, shape (6, Pz, Py, Px//2+1), complex numpy."""
     key = "Nhat"
     if key in p._cache:
         return p._cache[key]
@@ -106,7 +112,8 @@ def padded_tensor_spectrum(p):
     oy = np.arange(-(ny - 1), ny) % Py
     ox = np.arange(-(nx - 1), nx) % Px
     Npad[np.ix_(range(6), oz, oy, ox)] = full
-    Nhat = torch.fft.rfftn(torch.from_numpy(Npad), dim=(1, 2, 3))
+    del full
+    Nhat = sfft.rfftn(Npad, axes=(1, 2, 3), workers=_workers())
     p._cache[key] = Nhat
     return Nhat
 
@@ -115,20 +122,45 @@ _PAIRS = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (0, 1): 3, (1, 0): 3,
           (0, 2): 4, (2, 0): 4, (1, 2): 5, (2, 1): 5}
 
 
-def demag_field(p, m):
-    """H_d by zero-padded FFT convolution (exact linear convolution)."""
+def _convolve(p, M):
+    """-N * M for a (nz, ny, nx, 3) numpy field M (exact linear convolution by
+    zero padding to twice the grid)."""
     nx, ny, nz = p.nx, p.ny, p.nz
     Px, Py, Pz = 2 * nx, 2 * ny, 2 * nz
-    M = ms_field(p)[..., None] * m
-    Mpad = torch.zeros((3, Pz, Py, Px), dtype=DT)
-    Mpad[:, :nz, :ny, :nx] = M.permute(3, 0, 1, 2)
-    Mhat = torch.fft.rfftn(Mpad, dim=(1, 2, 3))
+    Mpad = np.zeros((3, Pz, Py, Px))
+    Mpad[:, :nz, :ny, :nx] = np.moveaxis(M, -1, 0)
+    Mhat = sfft.rfftn(Mpad, axes=(1, 2, 3), workers=_workers())
+    del Mpad
     Nhat = padded_tensor_spectrum(p)
-    H = torch.empty((nz, ny, nx, 3), dtype=DT)
+    H = np.empty((nz, ny, nx, 3))
     for i in range(3):
         Hhat = -sum(Nhat[_PAIRS[(i, j)]] * Mhat[j] for j in range(3))
-        H[..., i] = torch.fft.irfftn(Hhat, s=(Pz, Py, Px), dim=(0, 1, 2))[:nz, :ny, :nx]
+        H[..., i] = sfft.irfftn(Hhat, s=(Pz, Py, Px), axes=(0, 1, 2), workers=_workers())[:nz, :ny, :nx]
     return H
+
+
+class _DemagOp(torch.autograd.Function):
+    """H_d = -N * (Ms m).  Forward is the plain FFT convolution.  Backward (used
+    only by the discrete adjoint) relies on the convolution being self-adjoint,
+    N_ij(-R) = N_ji(R), which the oracle's symmetry pin checks."""
+
+    @staticmethod
+    def forward(ctx, m, Ms, p):
+        ctx.p = p
+        ctx.save_for_backward(m, Ms)
+        M = (Ms[..., None] * m).detach().numpy()
+        return torch.from_numpy(_convolve(p, M))
+
+    @staticmethod
+    def backward(ctx, g):
+        m, Ms = ctx.saved_tensors
+        u = torch.from_numpy(_convolve(ctx.p, g.detach().numpy()))
+        return Ms[..., None] * u, (m * u).sum(-1), None
+
+
+def demag_field(p, m):
+    """H_d by zero-padded FFT convolution (exact linear convolution)."""
+    return _DemagOp.apply(m, ms_field(p).contiguous(), p)
 
 
 def demag_field_direct(p, m):

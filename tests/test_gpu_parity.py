@@ -68,7 +68,7 @@ def test_tensor_spectrum_matches_oracle(name):
 
 
 def p_spectrum(p):
-    Nh = mm.padded_tensor_spectrum(p).numpy()  # (6, Pz, Py, Px/2+1)
+    Nh = mm.padded_tensor_spectrum(p)  # (6, Pz, Py, Px/2+1)
     assert np.abs(Nh.imag).max() <= 1e-12 * np.abs(Nh.real).max()
     Oz, Oy = Nh.shape[1] // 2 + 1, Nh.shape[2] // 2 + 1
     return Nh.real[:, :Oz, :Oy, :]
