@@ -184,6 +184,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   alloc((void**)&ctx->nhat, sizeof(float) * 6 * no);
   alloc((void**)&ctx->w1, sizeof(float2) * 3 * (long)g.nz * g.ny * g.Hx);
   alloc((void**)&ctx->tw_x, sizeof(float2) * g.Px);
+  alloc((void**)&ctx->tw_m, sizeof(float2) * (g.Px > 1 ? g.Px / 2 : 1));
   alloc((void**)&ctx->tw_y, sizeof(float2) * g.Py);
   alloc((void**)&ctx->tw_z, sizeof(float2) * g.Pz);
   alloc((void**)&ctx->hd, sizeof(float4) * nc);
@@ -194,6 +195,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   alloc((void**)&ctx->ered, sizeof(double) * 5);
   mx_status st = MX_OK;
   if (ok) st = demag_setup(ctx);
+  if (ok && st == MX_OK) st = fast_setup(ctx);
   if (ok && st == MX_OK && !ctx->fused_yz) alloc((void**)&ctx->w2, sizeof(float2) * 3 * (long)g.nz * g.Py * g.Hx);
   if (!ok) {
     mx_destroy(ctx);
@@ -205,7 +207,10 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
     return st;
   }
   std::vector<float2> tx = twiddles32(g.Px), ty = twiddles32(g.Py), tz = twiddles32(g.Pz);
+  const int Mx = g.Px > 1 ? g.Px / 2 : 1;
+  std::vector<float2> tm = twiddles32(Mx);
   if (cudaMemcpy(ctx->tw_x, tx.data(), sizeof(float2) * g.Px, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->tw_m, tm.data(), sizeof(float2) * Mx, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->tw_y, ty.data(), sizeof(float2) * g.Py, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->tw_z, tz.data(), sizeof(float2) * g.Pz, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(ctx->flag, 0, sizeof(int)) != cudaSuccess ||
@@ -221,7 +226,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
 mx_status mx_destroy(mx_ctx* ctx) {
   if (!ctx) return MX_OK;
   invalidate_graph(ctx);
-  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_y,
+  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_y,
                   ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered};
   for (void* q : ptrs)
     if (q) cudaFree(q);

@@ -321,9 +321,13 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
   const size_t xs = sizeof(float2) * 3 * rows * M;
   {
     ProfScope ps(ctx, KID_X_FWD, st);
-    x_fwd_kernel<<<(nrows + rows - 1) / rows, kNT, xs, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1,
-                                                             ctx->tw_x, rows);
-    MX_TRY(launch_check("x_fwd_kernel"));
+    if (ctx->fast_x) {
+      MX_TRY(fast_x_pass(ctx, m, nullptr, false, st));
+    } else {
+      x_fwd_kernel<<<(nrows + rows - 1) / rows, kNT, xs, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1,
+                                                               ctx->tw_x, rows);
+      MX_TRY(launch_check("x_fwd_kernel"));
+    }
   }
   if (ctx->fused_yz) {
     const int T = ctx->yz_tile;
@@ -331,6 +335,8 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
     ProfScope ps(ctx, KID_YZ, st);
     yz_fused_kernel<<<(g.Hx + T - 1) / T, kNT, s, st>>>(ctx->w1, g, ctx->nhat, ctx->tw_y, ctx->tw_z, T);
     MX_TRY(launch_check("yz_fused_kernel"));
+  } else if (ctx->fast_yz) {
+    MX_TRY(fast_yz_passes(ctx, st));
   } else {
     const int Ty = col_tile(g.Py);
     const int nty = (g.Hx + Ty - 1) / Ty;
@@ -354,8 +360,12 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
   }
   {
     ProfScope ps(ctx, KID_X_INV, st);
-    x_inv_kernel<<<(nrows + rows - 1) / rows, kNT, xs, st>>>(ctx->w1, g, hd, ctx->tw_x, rows);
-    MX_TRY(launch_check("x_inv_kernel"));
+    if (ctx->fast_x) {
+      MX_TRY(fast_x_pass(ctx, nullptr, hd, true, st));
+    } else {
+      x_inv_kernel<<<(nrows + rows - 1) / rows, kNT, xs, st>>>(ctx->w1, g, hd, ctx->tw_x, rows);
+      MX_TRY(launch_check("x_inv_kernel"));
+    }
   }
   return MX_OK;
 }

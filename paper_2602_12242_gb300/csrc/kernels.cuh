@@ -34,6 +34,11 @@ struct ProfScope {
 mx_status demag_setup(mx_ctx* ctx);
 mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st);
 
+// demag_fast.cu
+mx_status fast_setup(mx_ctx* ctx);
+mx_status fast_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st);
+mx_status fast_yz_passes(mx_ctx* ctx, cudaStream_t st);
+
 // newell.cu
 mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st);
 
