@@ -67,6 +67,11 @@ typedef enum {
  *           0: no DMI, Neumann boundaries
  *   precession 1: full LLG; 0: damping term only (relaxation)
  *   demag   1: include the demagnetising field
+ *   demag_path  schedule of the demag convolution (same result up to FP32
+ *           rounding): MX_DEMAG_AUTO picks the fastest that fits the grid;
+ *           MX_DEMAG_GENERIC forces the size-generic separate passes;
+ *           MX_DEMAG_PLANE forces the per-kx-plane kernel (MX_ERR_UNSUPPORTED
+ *           at mx_create if the grid does not fit it)
  */
 typedef struct {
     int nx, ny, nz;
@@ -77,7 +82,11 @@ typedef struct {
     int dmi_interfacial;
     int precession;
     int demag;
+    int demag_path;
 } mx_params;
+
+/* Demag convolution schedules for mx_params.demag_path. */
+enum { MX_DEMAG_AUTO = 0, MX_DEMAG_GENERIC = 1, MX_DEMAG_PLANE = 2 };
 
 /* Field terms, for mx_heff's term mask. */
 enum {

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "MX_OK", 1: "MX_ERR_INVALID_ARG", 2: "MX_ERR_CUDA", 3: "MX_ER
 MX_TERM_DEMAG, MX_TERM_EXCH, MX_TERM_ANIS, MX_TERM_DMI, MX_TERM_ZEEMAN = 1, 2, 4, 8, 16
 MX_TERM_ALL = 31
 MX_RK4, MX_EULER = 0, 1
+MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE = 0, 1, 2
 
 
 class MxError(RuntimeError):
@@ -34,7 +35,8 @@ class mx_params(ctypes.Structure):
                 ("Ms", ctypes.c_double), ("A", ctypes.c_double), ("Ku", ctypes.c_double),
                 ("D", ctypes.c_double), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("ku_axis", ctypes.c_double * 3), ("h_bias", ctypes.c_double * 3),
-                ("dmi_interfacial", ctypes.c_int), ("precession", ctypes.c_int), ("demag", ctypes.c_int)]
+                ("dmi_interfacial", ctypes.c_int), ("precession", ctypes.c_int), ("demag", ctypes.c_int),
+                ("demag_path", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

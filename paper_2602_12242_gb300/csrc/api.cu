@@ -153,6 +153,10 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
     set_error("mx_create: need dx, dy, dz, Ms, gamma > 0 and A, alpha >= 0");
     return MX_ERR_INVALID_ARG;
   }
+  if (p->demag_path < MX_DEMAG_AUTO || p->demag_path > MX_DEMAG_PLANE) {
+    set_error("mx_create: demag_path must be MX_DEMAG_AUTO, MX_DEMAG_GENERIC or MX_DEMAG_PLANE");
+    return MX_ERR_INVALID_ARG;
+  }
   if (p->dmi_interfacial && p->D != 0.0 && !(p->A > 0)) {
     set_error("mx_create: DMI boundary condition needs A > 0");
     return MX_ERR_INVALID_ARG;
@@ -186,6 +190,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   alloc((void**)&ctx->tw_x, sizeof(float2) * g.Px);
   alloc((void**)&ctx->tw_m, sizeof(float2) * (g.Px > 1 ? g.Px / 2 : 1));
   alloc((void**)&ctx->tw_y, sizeof(float2) * g.Py);
+  alloc((void**)&ctx->tw_yh, sizeof(float2) * (g.Py > 1 ? g.Py / 2 : 1));
   alloc((void**)&ctx->tw_z, sizeof(float2) * g.Pz);
   alloc((void**)&ctx->hd, sizeof(float4) * nc);
   alloc((void**)&ctx->sa, sizeof(float4) * nc);
@@ -196,6 +201,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   mx_status st = MX_OK;
   if (ok) st = demag_setup(ctx);
   if (ok && st == MX_OK) st = fast_setup(ctx);
+  if (ok && st == MX_OK) st = plane_setup(ctx);
   if (ok && st == MX_OK && !ctx->fused_yz) alloc((void**)&ctx->w2, sizeof(float2) * 3 * (long)g.nz * g.Py * g.Hx);
   if (!ok) {
     mx_destroy(ctx);
@@ -209,8 +215,11 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   std::vector<float2> tx = twiddles32(g.Px), ty = twiddles32(g.Py), tz = twiddles32(g.Pz);
   const int Mx = g.Px > 1 ? g.Px / 2 : 1;
   std::vector<float2> tm = twiddles32(Mx);
+  const int Hy = g.Py > 1 ? g.Py / 2 : 1;
+  std::vector<float2> th = twiddles32(Hy);
   if (cudaMemcpy(ctx->tw_x, tx.data(), sizeof(float2) * g.Px, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->tw_m, tm.data(), sizeof(float2) * Mx, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->tw_yh, th.data(), sizeof(float2) * Hy, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->tw_y, ty.data(), sizeof(float2) * g.Py, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->tw_z, tz.data(), sizeof(float2) * g.Pz, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(ctx->flag, 0, sizeof(int)) != cudaSuccess ||
@@ -226,7 +235,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
 mx_status mx_destroy(mx_ctx* ctx) {
   if (!ctx) return MX_OK;
   invalidate_graph(ctx);
-  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_y,
+  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_yh, ctx->tw_y,
                   ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -496,6 +505,7 @@ mx_status mx_demag_spectrum(mx_ctx* ctx, float* out, mx_stream_t stream) {
     set_error("mx_demag_spectrum: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
+  if (ctx->plane) return plane_spectrum_out(ctx, out, (cudaStream_t)stream);
   const long no = (long)ctx->g.Hx * ctx->g.Oy * ctx->g.Oz;
   MX_CUDA_TRY(cudaMemcpyAsync(out, ctx->nhat, sizeof(float) * 6 * no, cudaMemcpyDeviceToDevice,
                               (cudaStream_t)stream));

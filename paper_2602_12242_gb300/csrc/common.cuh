@@ -120,8 +120,9 @@ struct mx_ctx {
   float2* tw_z = nullptr;         // W_Pz^k, k < Pz
   bool fused_yz = false;          // y/z passes in one kernel (plane fits on chip)
   bool fast_x = false;            // compile-time-sized x passes available
-  bool fast_yz = false;           // compile-time-sized y / z passes available
   float2* tw_m = nullptr;         // W_M^k, k < M = Px/2
+  float2* tw_yh = nullptr;        // W_{Py/2}^k, k < Py/2
+  bool plane = false;             // per-kx plane kernel (kx-major spectra and tensor)
   int yz_tile = 1;                // kx columns per block in the fused kernel
   double* t_real = nullptr;       // FP64 real-space tensor octant (kept for checking)
   double spectrum_imag_ratio = 0; // max|Im| / max|Re| of the FP64 tensor spectrum

@@ -301,7 +301,8 @@ mx_status demag_setup(mx_ctx* ctx) {
   int T = kCap / (3 * g.Py * g.Pz);
   while (T > 1 && (size_t)3 * g.Py * g.Pz * T * sizeof(float2) > 96 * 1024) --T;
   if (T > 16) T = 16;
-  ctx->fused_yz = (T >= 1) && (3L * g.Py * g.Pz <= kCap) && (size_t)3 * g.Py * g.Pz * sizeof(float2) <= 96 * 1024;
+  ctx->fused_yz = ctx->p.demag_path == MX_DEMAG_AUTO && (T >= 1) && (3L * g.Py * g.Pz <= kCap) &&
+                  (size_t)3 * g.Py * g.Pz * sizeof(float2) <= 96 * 1024;
   ctx->yz_tile = T < 1 ? 1 : T;
   const int big = 200 * 1024;
   MX_CUDA_TRY(cudaFuncSetAttribute(x_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -314,6 +315,7 @@ mx_status demag_setup(mx_ctx* ctx) {
 }
 
 mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st) {
+  if (ctx->plane) return plane_field(ctx, m, hd, st);
   const Grid& g = ctx->g;
   const int rows = x_rows(g);
   const int nrows = g.ny * g.nz;
@@ -335,8 +337,6 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
     ProfScope ps(ctx, KID_YZ, st);
     yz_fused_kernel<<<(g.Hx + T - 1) / T, kNT, s, st>>>(ctx->w1, g, ctx->nhat, ctx->tw_y, ctx->tw_z, T);
     MX_TRY(launch_check("yz_fused_kernel"));
-  } else if (ctx->fast_yz) {
-    MX_TRY(fast_yz_passes(ctx, st));
   } else {
     const int Ty = col_tile(g.Py);
     const int nty = (g.Hx + Ty - 1) / Ty;

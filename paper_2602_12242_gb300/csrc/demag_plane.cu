@@ -1,0 +1,393 @@
+// Demag convolution for large grids with one kernel per kx plane (Sec. II-B:
+// zero-padded FFT convolution with the tensor spectrum; the arithmetic is the
+// same as demag.cu, only the schedule differs).
+//
+// Spectra use a kx-major layout, w[kx][c][z][y] (y fastest), so a kx plane is
+// contiguous.  The tensor octant is stored the same way, nhat[kx][comp][qz][qy].
+//
+//   xfk  r2c along x for R consecutive rows (same z); the spectrum is
+//        transposed in shared memory so the kx-major stores are coalesced.
+//   yzh  one block per kx: the y transform of the zero-padded column (only the
+//        first ny <= Py/2 inputs non-zero) splits into its even outputs, an
+//        Py/2-point FFT of x, and its odd outputs, an Py/2-point FFT of
+//        x W_Py^y.  The block runs the two halves one after the other; each
+//        holds [c][z][Py/2] in shared memory: forward y FFT, then per ky the
+//        z FFT, the 3x3 tensor multiply and the inverse z FFT (four lanes per
+//        column, one residue class kz mod 4 each), then the inverse y FFT.  The
+//        inverse y transform restricted to y < ny is the sum of the two
+//        halves' inverses, the odd one times W_Py^-y: the even half is stored
+//        and the odd half is added to it.
+//   xik  c2r along x for R consecutive rows, reading the kx-major spectrum.
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels.cuh"
+#include "regfft.cuh"
+
+namespace mx {
+
+constexpr int kRows = 8;      // rows per block in xfk / xik
+constexpr int kPlaneNT = 512; // threads per yzh block
+
+// ---------------------------------------------------------------------------
+// x forward into the kx-major spectrum.
+// ---------------------------------------------------------------------------
+template <int E, int S>
+__global__ void __launch_bounds__(3 * kRows * S) xfk_kernel(const float4* __restrict__ m, Grid g, float ms,
+                                                            const float* __restrict__ ms_map, float2* __restrict__ w1,
+                                                            const float2* __restrict__ twM,
+                                                            const float2* __restrict__ twP) {
+  constexpr int M = E * S;
+  constexpr int P = LineFft<E, S>::kPitch + 1;
+  constexpr int NT = 3 * kRows * S;
+  extern __shared__ float2 sm[];
+  const int ychunks = (g.ny + kRows - 1) / kRows;
+  const int z = blockIdx.x / ychunks;
+  const int y0 = (blockIdx.x % ychunks) * kRows;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kRows * M; e += NT) {
+    const int r = e / M, n = e % M;
+    const int y = y0 + r;
+    float2 zx = make_float2(0.f, 0.f), zy = zx, zz = zx;
+    if (y < g.ny) {
+      const long cell = ((long)z * g.ny + y) * g.nx;
+      const int i0 = 2 * n, i1 = i0 + 1;
+      if (i0 < g.nx) {
+        const float4 a = __ldg(&m[cell + i0]);
+        const float s = ms_map ? __ldg(&ms_map[cell + i0]) : ms;
+        zx.x = s * a.x; zy.x = s * a.y; zz.x = s * a.z;
+      }
+      if (i1 < g.nx) {
+        const float4 b = __ldg(&m[cell + i1]);
+        const float s = ms_map ? __ldg(&ms_map[cell + i1]) : ms;
+        zx.y = s * b.x; zy.y = s * b.y; zz.y = s * b.z;
+      }
+    }
+    sm[(3 * r + 0) * P + n] = zx;
+    sm[(3 * r + 1) * P + n] = zy;
+    sm[(3 * r + 2) * P + n] = zz;
+  }
+  __syncthreads();
+  line_fft<E, S, false>(sm + (tid / S) * P, tid % S, twM);
+  __syncthreads();
+  const long plane = 3L * g.nz * g.ny;  // one kx
+  for (int e = tid; e < 3 * kRows * (M + 1); e += NT) {
+    const int r = e % kRows;
+    const int c = (e / kRows) % 3;
+    const int k = e / (3 * kRows);
+    const int y = y0 + r;
+    if (y >= g.ny) continue;
+    const float2* L = sm + (3 * r + c) * P;
+    const float2 zk = L[k == M ? 0 : k];
+    const float2 zc = cconj(L[k == 0 ? 0 : M - k]);
+    const float2 Ev = cscale(cadd(zk, zc), 0.5f);
+    const float2 D = csub(zk, zc);
+    const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+    w1[(long)k * plane + ((long)c * g.nz + z) * g.ny + y] = cadd(Ev, cmul(__ldg(&twP[k]), O));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x inverse from the kx-major spectrum.
+// ---------------------------------------------------------------------------
+template <int E, int S>
+__global__ void __launch_bounds__(3 * kRows * S) xik_kernel(const float2* __restrict__ w2, Grid g,
+                                                            float4* __restrict__ hd, const float2* __restrict__ twM,
+                                                            const float2* __restrict__ twP) {
+  constexpr int M = E * S;
+  constexpr int P = LineFft<E, S>::kPitch + 1;
+  constexpr int NT = 3 * kRows * S;
+  extern __shared__ float2 sm[];
+  const int ychunks = (g.ny + kRows - 1) / kRows;
+  const int z = blockIdx.x / ychunks;
+  const int y0 = (blockIdx.x % ychunks) * kRows;
+  const int tid = threadIdx.x;
+  const long plane = 3L * g.nz * g.ny;
+  for (int e = tid; e < 3 * kRows * M; e += NT) {
+    const int r = e % kRows;
+    const int c = (e / kRows) % 3;
+    const int k = e / (3 * kRows);
+    const int y = y0 + r;
+    float2 v = make_float2(0.f, 0.f);
+    if (y < g.ny) {
+      const long o = ((long)c * g.nz + z) * g.ny + y;
+      const float2 a = __ldg(&w2[(long)k * plane + o]);
+      const float2 b = cconj(__ldg(&w2[(long)(M - k) * plane + o]));
+      const float2 Sv = cadd(a, b);
+      const float2 t = cmul(cconj(__ldg(&twP[k])), csub(a, b));
+      v = make_float2(Sv.x - t.y, Sv.y + t.x);
+    }
+    sm[(3 * r + c) * P + k] = v;
+  }
+  __syncthreads();
+  line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
+  __syncthreads();
+  for (int e = tid; e < kRows * g.nx; e += NT) {
+    const int r = e / g.nx, i = e % g.nx;
+    const int y = y0 + r;
+    if (y >= g.ny) continue;
+    const float2* L = sm + (3 * r) * P;
+    const int n = i >> 1;
+    const bool odd = i & 1;
+    const float hx = odd ? L[n].y : L[n].x;
+    const float hy = odd ? L[P + n].y : L[P + n].x;
+    const float hz = odd ? L[2 * P + n].y : L[2 * P + n].x;
+    hd[((long)z * g.ny + y) * g.nx + i] = make_float4(hx, hy, hz, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-kx plane: y FFT halves, z FFT + multiply + inverse z, inverse y.
+// ---------------------------------------------------------------------------
+template <int E, int S, int P>
+__global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restrict__ w1, float2* __restrict__ w2,
+                                                          Grid g, const float* __restrict__ nhk,
+                                                          const float2* __restrict__ twPy,
+                                                          const float2* __restrict__ twH,
+                                                          const float2* __restrict__ twz) {
+  constexpr int LH = E * S;                       // Py / 2
+  constexpr int PITCH = LineFft<E, S>::kPitch;
+  constexpr int Q = P / 4;                        // points per residue class of kz
+  constexpr int NT = kPlaneNT;
+  extern __shared__ float2 sm[];
+  const int kx = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int nz = g.nz, ny = g.ny;
+  const int nlines = 3 * nz;
+  const long kxoff = (long)kx * nlines * ny;
+  float2* dummy = sm + nlines * PITCH;            // scratch line for idle groups
+  const float* nk = nhk + (long)kx * 6 * g.Oz * g.Oy;
+  const long cst = (long)g.Oz * g.Oy;
+
+  for (int h = 0; h < 2; ++h) {
+    for (int e = tid; e < nlines * LH; e += NT) {
+      const int line = e / LH, y = e % LH;
+      float2 v = make_float2(0.f, 0.f);
+      if (y < ny) {
+        v = __ldg(&w1[kxoff + (long)line * ny + y]);
+        if (h) v = cmul(v, __ldg(&twPy[y]));
+      }
+      sm[line * PITCH + y] = v;
+    }
+    __syncthreads();
+    for (int l0 = 0; l0 < nlines; l0 += NT / S) {
+      const int l = l0 + tid / S;
+      line_fft<E, S, false>(l < nlines ? sm + l * PITCH : dummy, tid % S, twH);
+    }
+    __syncthreads();
+    // z stage: 4 lanes per ky column, lane r owns kz = 4q + r
+    for (int task = tid; task < 4 * LH; task += NT) {
+      const int kyh = task >> 2, r = task & 3;
+      const int ky = 2 * kyh + h;
+      const bool fy = ky > (g.Py >> 1);
+      const int qy = fy ? g.Py - ky : ky;
+      float2 Z[3][Q];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int n = 0; n < Q; ++n) {
+          float2 a = make_float2(0.f, 0.f), b = a;
+          if (n < nz) a = sm[(c * nz + n) * PITCH + kyh];
+          if (n + Q < nz) b = sm[(c * nz + n + Q) * PITCH + kyh];
+          // y_r[n] = x[n] W_P^(r n) + x[n + Q] W_P^(r (n + Q))
+          const float2 wa = __ldg(&twz[(r * n) % P]);
+          const float2 wb = __ldg(&twz[(r * (n + Q)) % P]);
+          Z[c][n] = cadd(cmul(a, wa), cmul(b, wb));
+        }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) RegFft<Q, false>::run(Z[c]);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int kz = 4 * q + r;
+        const bool fz = kz > (P >> 1);
+        const int qz = fz ? P - kz : kz;
+        const long o = (long)qz * g.Oy + qy;
+        const float nxx = __ldg(&nk[o]), nyy = __ldg(&nk[cst + o]), nzz = __ldg(&nk[2 * cst + o]);
+        const float nxy = (fy ? -1.f : 1.f) * __ldg(&nk[3 * cst + o]);
+        const float nxz = (fz ? -1.f : 1.f) * __ldg(&nk[4 * cst + o]);
+        const float nyz = ((fy != fz) ? -1.f : 1.f) * __ldg(&nk[5 * cst + o]);
+        const float2 mx = Z[0][q], my = Z[1][q], mz = Z[2][q];
+        Z[0][q] = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
+        Z[1][q] = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
+        Z[2][q] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) RegFft<Q, true>::run(Z[c]);
+      // x[n] = sum_r W_P^(-r n) u_r[n mod Q] for n < 2Q, summed over the 4 lanes:
+      // xor 2 leaves each lane pair one half [hb, hb + Q), xor 1 one quarter
+      const int hb = (r >> 1) * Q;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 sacc[Q];
+#pragma unroll
+        for (int n = 0; n < Q; ++n) {
+          const float2 lo = cmul(Z[c][n], cconj(__ldg(&twz[(r * n) % P])));        // term n
+          const float2 hi = cmul(Z[c][n], cconj(__ldg(&twz[(r * (n + Q)) % P])));  // term n + Q
+          const float2 keep = (r >> 1) ? hi : lo;
+          const float2 give = (r >> 1) ? lo : hi;
+          float2 o;
+          o.x = __shfl_xor_sync(0xffffffffu, give.x, 2);
+          o.y = __shfl_xor_sync(0xffffffffu, give.y, 2);
+          sacc[n] = cadd(keep, o);
+        }
+        if constexpr (Q >= 2) {
+#pragma unroll
+          for (int n = 0; n < Q / 2; ++n) {
+            const float2 keep = (r & 1) ? sacc[n + Q / 2] : sacc[n];
+            const float2 give = (r & 1) ? sacc[n] : sacc[n + Q / 2];
+            float2 o;
+            o.x = __shfl_xor_sync(0xffffffffu, give.x, 1);
+            o.y = __shfl_xor_sync(0xffffffffu, give.y, 1);
+            const int idx = hb + (r & 1) * (Q / 2) + n;
+            if (idx < nz) sm[(c * nz + idx) * PITCH + kyh] = cadd(keep, o);
+          }
+        } else {
+          float2 o;
+          o.x = __shfl_xor_sync(0xffffffffu, sacc[0].x, 1);
+          o.y = __shfl_xor_sync(0xffffffffu, sacc[0].y, 1);
+          if ((r & 1) == 0 && hb < nz) sm[(c * nz + hb) * PITCH + kyh] = cadd(sacc[0], o);
+        }
+      }
+    }
+    __syncthreads();
+    for (int l0 = 0; l0 < nlines; l0 += NT / S) {
+      const int l = l0 + tid / S;
+      line_fft<E, S, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twH);
+    }
+    __syncthreads();
+    for (int e = tid; e < nlines * ny; e += NT) {
+      const int line = e / ny, y = e % ny;
+      float2 v = sm[line * PITCH + y];
+      const long o = kxoff + (long)line * ny + y;
+      if (h == 0) {
+        w2[o] = v;
+      } else {
+        v = cmul(v, cconj(__ldg(&twPy[y])));
+        w2[o] = cadd(w2[o], v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <int E, int S> static size_t xk_smem() { return sizeof(float2) * 3 * kRows * (LineFft<E, S>::kPitch + 1); }
+template <int E, int S> static size_t yzh_smem(int nz) {
+  return sizeof(float2) * (3 * nz + 1) * LineFft<E, S>::kPitch;
+}
+
+template <int E, int S>
+static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
+  const size_t sm = xk_smem<E, S>();
+  if (setup) {
+    MX_CUDA_TRY(cudaFuncSetAttribute(xfk_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(xik_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return MX_OK;
+  }
+  const Grid& g = ctx->g;
+  const int nblk = g.nz * ((g.ny + kRows - 1) / kRows);
+  if (!inverse) {
+    xfk_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, ctx->tw_m,
+                                                       ctx->tw_x);
+    return launch_check("xfk_kernel");
+  }
+  xik_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(ctx->w2, g, hd, ctx->tw_m, ctx->tw_x);
+  return launch_check("xik_kernel");
+}
+
+template <int E, int S, int P>
+static mx_status yzh_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
+  const Grid& g = ctx->g;
+  const size_t sm = yzh_smem<E, S>(g.nz);
+  if (setup) {
+    if (sm > 227 * 1024) return MX_ERR_UNSUPPORTED;
+    MX_CUDA_TRY(cudaFuncSetAttribute(yzh_kernel<E, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return MX_OK;
+  }
+  yzh_kernel<E, S, P><<<g.Hx, kPlaneNT, sm, st>>>(ctx->w1, ctx->w2, g, ctx->nhat, ctx->tw_y, ctx->tw_yh, ctx->tw_z);
+  return launch_check("yzh_kernel");
+}
+
+static mx_status xk_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
+  switch (ctx->g.Px / 2) {
+    case 1024: return xk_run<32, 32>(ctx, m, hd, inverse, st, setup);
+    case 512: return xk_run<32, 16>(ctx, m, hd, inverse, st, setup);
+    case 256: return xk_run<16, 16>(ctx, m, hd, inverse, st, setup);
+    case 128: return xk_run<16, 8>(ctx, m, hd, inverse, st, setup);
+    case 64: return xk_run<8, 8>(ctx, m, hd, inverse, st, setup);
+    default: return MX_ERR_UNSUPPORTED;
+  }
+}
+
+template <int E, int S>
+static mx_status yzh_pz(mx_ctx* ctx, cudaStream_t st, bool setup) {
+  switch (ctx->g.Pz) {
+    case 32: return yzh_run<E, S, 32>(ctx, st, setup);
+    case 16: return yzh_run<E, S, 16>(ctx, st, setup);
+    case 8: return yzh_run<E, S, 8>(ctx, st, setup);
+    case 4: return yzh_run<E, S, 4>(ctx, st, setup);
+    default: return MX_ERR_UNSUPPORTED;
+  }
+}
+
+static mx_status yzh_pass(mx_ctx* ctx, cudaStream_t st, bool setup) {
+  switch (ctx->g.Py / 2) {
+    case 1024: return yzh_pz<32, 32>(ctx, st, setup);
+    case 512: return yzh_pz<32, 16>(ctx, st, setup);
+    case 256: return yzh_pz<16, 16>(ctx, st, setup);
+    case 128: return yzh_pz<16, 8>(ctx, st, setup);
+    case 64: return yzh_pz<8, 8>(ctx, st, setup);
+    case 32: return yzh_pz<32, 1>(ctx, st, setup);
+    case 16: return yzh_pz<16, 1>(ctx, st, setup);
+    default: return MX_ERR_UNSUPPORTED;
+  }
+}
+
+mx_status plane_setup(mx_ctx* ctx) {
+  MX_TRY(upload_w32());
+  const int path = ctx->p.demag_path;
+  ctx->plane = path != MX_DEMAG_GENERIC && !ctx->fused_yz &&
+               xk_pass(ctx, nullptr, nullptr, false, nullptr, true) == MX_OK &&
+               yzh_pass(ctx, nullptr, true) == MX_OK;
+  clear_error();
+  if (path == MX_DEMAG_PLANE && !ctx->plane) {
+    set_error("mx_create: the per-kx plane demag kernel does not support this grid");
+    return MX_ERR_UNSUPPORTED;
+  }
+  return MX_OK;
+}
+
+mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st) {
+  {
+    ProfScope ps(ctx, KID_X_FWD, st);
+    MX_TRY(xk_pass(ctx, m, nullptr, false, st, false));
+  }
+  {
+    ProfScope ps(ctx, KID_YZ, st);
+    MX_TRY(yzh_pass(ctx, st, false));
+  }
+  {
+    ProfScope ps(ctx, KID_X_INV, st);
+    MX_TRY(xk_pass(ctx, nullptr, hd, true, st, false));
+  }
+  return MX_OK;
+}
+
+// kx-major octant [kx][comp][qz][qy] <-> [comp][qz][qy][kx]
+__global__ void octant_to_cmajor_kernel(const float* __restrict__ src, float* __restrict__ dst, Grid g) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long no = (long)g.Hx * g.Oy * g.Oz;
+  if (idx >= 6 * no) return;
+  const int kx = (int)(idx % g.Hx);
+  const long rest = idx / g.Hx;  // (comp, qz, qy)
+  dst[idx] = src[(long)kx * 6 * g.Oz * g.Oy + rest];
+}
+
+mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st) {
+  const long n = 6L * ctx->g.Hx * ctx->g.Oy * ctx->g.Oz;
+  octant_to_cmajor_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctx->nhat, out, ctx->g);
+  return launch_check("octant_to_cmajor_kernel");
+}
+
+}  // namespace mx

@@ -37,7 +37,11 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
 // demag_fast.cu
 mx_status fast_setup(mx_ctx* ctx);
 mx_status fast_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st);
-mx_status fast_yz_passes(mx_ctx* ctx, cudaStream_t st);
+
+// demag_plane.cu
+mx_status plane_setup(mx_ctx* ctx);
+mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st);
+mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 
 // newell.cu
 mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st);

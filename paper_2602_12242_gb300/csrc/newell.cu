@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kF64Threads) fft_axis_f64_kernel(double2* data
 // Keep the real part of the octant kx <= Px/2, ky <= Py/2, kz <= Pz/2,
 // scaled by -1/(Px Py Pz), in FP32.  Also record max |imag| / max |real| of
 // the whole spectrum (a check that the symmetric tensor's spectrum is real).
-__global__ void extract_octant_kernel(const double2* buf, int comp, Grid g, float* nhat,
+__global__ void extract_octant_kernel(const double2* buf, int comp, Grid g, float* nhat, int kxmajor,
                                       unsigned long long* max_re, unsigned long long* max_im) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long no = (long)g.Hx * g.Oy * g.Oz;
@@ -292,9 +292,24 @@ __global__ void extract_octant_kernel(const double2* buf, int comp, Grid g, floa
   const int kz = (int)(idx / ((long)g.Hx * g.Oy));
   const double2 v = buf[((long)kz * g.Py + ky) * g.Px + kx];
   const double scale = -1.0 / ((double)g.Px * g.Py * g.Pz);
-  nhat[(long)comp * no + idx] = (float)(v.x * scale);
-  atomicMax(max_re, (unsigned long long)__double_as_longlong(fabs(v.x)));
-  atomicMax(max_im, (unsigned long long)__double_as_longlong(fabs(v.y)));
+  const long dst = kxmajor ? (((long)kx * 6 + comp) * g.Oz + kz) * g.Oy + ky : (long)comp * no + idx;
+  nhat[dst] = (float)(v.x * scale);
+  // warp maxima first, then one atomic per warp
+  unsigned long long re = (unsigned long long)__double_as_longlong(fabs(v.x));
+  unsigned long long im = (unsigned long long)__double_as_longlong(fabs(v.y));
+  const unsigned mask = __activemask();
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long r2 = __shfl_down_sync(mask, re, o);
+    const unsigned long long i2 = __shfl_down_sync(mask, im, o);
+    if ((threadIdx.x & 31) + o < 32 && ((mask >> ((threadIdx.x & 31) + o)) & 1)) {
+      re = r2 > re ? r2 : re;
+      im = i2 > im ? i2 : im;
+    }
+  }
+  if ((threadIdx.x & 31) == (__ffs(mask) - 1)) {
+    atomicMax(max_re, re);
+    atomicMax(max_im, im);
+  }
 }
 
 static mx_status fft3_f64(double2* buf, const Grid& g, const double2* twx, const double2* twy,
@@ -361,7 +376,8 @@ mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st) {
       if (status == MX_OK) status = fft3_f64(buf, g, tw, tw + g.Px, tw + g.Px + g.Py, st);
       if (status == MX_OK) {
         const long no = (long)g.Hx * g.Oy * g.Oz;
-        extract_octant_kernel<<<(unsigned)((no + 255) / 256), 256, 0, st>>>(buf, c, g, ctx->nhat, mx, mx + 1);
+        extract_octant_kernel<<<(unsigned)((no + 255) / 256), 256, 0, st>>>(buf, c, g, ctx->nhat, ctx->plane ? 1 : 0,
+                                                                             mx, mx + 1);
         status = launch_check("extract_octant_kernel");
       }
     }

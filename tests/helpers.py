@@ -23,10 +23,10 @@ def problem(cfg, Ms=None, Ku=None, axis=None, demag=True, precession=True):
                       precession=precession)
 
 
-def context(cfg, Ms=None, Ku=None, axis=None, demag=True):
+def context(cfg, Ms=None, Ku=None, axis=None, demag=True, demag_path=0):
     from paper_2602_12242_gb300.solver import Context
     c = dict(cfg)
-    return Context.from_config(c, Ms=Ms, Ku=Ku, ku_axis=axis, demag=demag)
+    return Context.from_config(c, Ms=Ms, Ku=Ku, ku_axis=axis, demag=demag, demag_path=demag_path)
 
 
 def rel_l2(a, b):

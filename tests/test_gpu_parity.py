@@ -274,3 +274,24 @@ def test_bulk_workload_full_size_sampled_direct_sum():
     ctx.sync()
     nrm = np.linalg.norm(host(dm), axis=-1)
     assert np.abs(nrm - 1).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["tall64x512x16", "mid40x300x3", "ragged37x21x5", "film17x9", "cell1"])
+@pytest.mark.parametrize("path", ["generic", "plane"])
+def test_each_demag_schedule_matches_oracle(name, path):
+    """Every schedule of the convolution (size-generic passes, per-kx plane kernel)
+    gives the oracle's field; grids the plane kernel cannot take are refused."""
+    from paper_2602_12242_gb300 import MX_TERM_DEMAG, MxError, _lib
+    c = CASES[name]
+    code = {"generic": _lib.MX_DEMAG_GENERIC, "plane": _lib.MX_DEMAG_PLANE}[path]
+    try:
+        ctx = context(c, demag_path=code)
+    except MxError as e:
+        assert path == "plane" and e.status == _lib.MX_ERR_UNSUPPORTED
+        assert name in ("cell1", "film17x9")  # Py/2 < 16 or Pz < 4
+        return
+    m = f32(random_m(c, 19))
+    h = host(ctx.heff(gpu_m(m), terms=MX_TERM_DEMAG))
+    ref = mm.demag_field(problem(c), t64(m)).numpy()
+    assert rel_l2(h, ref) <= TOL_FIELD
+    assert rel_max(h, ref) <= 1e-4
