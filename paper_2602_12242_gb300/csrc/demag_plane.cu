@@ -32,7 +32,7 @@ constexpr int kPlaneNT = 512; // threads per yzh block
 // x forward into the kx-major spectrum.
 // ---------------------------------------------------------------------------
 template <int E, int S>
-__global__ void __launch_bounds__(3 * kRows * S) xfk_kernel(const float4* __restrict__ m, Grid g, float ms,
+__global__ void __launch_bounds__(3 * kRows * S, 2) xfk_kernel(const float4* __restrict__ m, Grid g, float ms,
                                                             const float* __restrict__ ms_map, float2* __restrict__ w1,
                                                             const float2* __restrict__ twM,
                                                             const float2* __restrict__ twP) {
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(3 * kRows * S) xfk_kernel(const float4* __rest
 // x inverse from the kx-major spectrum.
 // ---------------------------------------------------------------------------
 template <int E, int S>
-__global__ void __launch_bounds__(3 * kRows * S) xik_kernel(const float2* __restrict__ w2, Grid g,
+__global__ void __launch_bounds__(3 * kRows * S, 2) xik_kernel(const float2* __restrict__ w2, Grid g,
                                                             float4* __restrict__ hd, const float2* __restrict__ twM,
                                                             const float2* __restrict__ twP) {
   constexpr int M = E * S;
@@ -155,8 +155,12 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
   const int nlines = 3 * nz;
   const long kxoff = (long)kx * nlines * ny;
   float2* dummy = sm + nlines * PITCH;            // scratch line for idle groups
+  float2* twS = dummy + PITCH;                    // W_LH^q, q < LH, in shared memory
   const float* nk = nhk + (long)kx * 6 * g.Oz * g.Oy;
   const long cst = (long)g.Oz * g.Oy;
+  float2* twZ = twS + LH;                         // W_P^(r n) for r < 4, n < 2Q
+  for (int q = tid; q < LH; q += NT) twS[q] = __ldg(&twH[q]);
+  for (int q = tid; q < 8 * Q; q += NT) twZ[q] = __ldg(&twz[((q / (2 * Q)) * (q % (2 * Q))) % P]);
 
   for (int h = 0; h < 2; ++h) {
     for (int e = tid; e < nlines * LH; e += NT) {
@@ -171,12 +175,13 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
     __syncthreads();
     for (int l0 = 0; l0 < nlines; l0 += NT / S) {
       const int l = l0 + tid / S;
-      line_fft<E, S, false>(l < nlines ? sm + l * PITCH : dummy, tid % S, twH);
+      line_fft<E, S, false, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
     }
     __syncthreads();
     // z stage: 4 lanes per ky column, lane r owns kz = 4q + r
     for (int task = tid; task < 4 * LH; task += NT) {
       const int kyh = task >> 2, r = task & 3;
+      const float2* wz = twZ + r * 2 * Q;
       const int ky = 2 * kyh + h;
       const bool fy = ky > (g.Py >> 1);
       const int qy = fy ? g.Py - ky : ky;
@@ -189,9 +194,7 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
           if (n < nz) a = sm[(c * nz + n) * PITCH + kyh];
           if (n + Q < nz) b = sm[(c * nz + n + Q) * PITCH + kyh];
           // y_r[n] = x[n] W_P^(r n) + x[n + Q] W_P^(r (n + Q))
-          const float2 wa = __ldg(&twz[(r * n) % P]);
-          const float2 wb = __ldg(&twz[(r * (n + Q)) % P]);
-          Z[c][n] = cadd(cmul(a, wa), cmul(b, wb));
+          Z[c][n] = cadd(cmul(a, wz[n]), cmul(b, wz[n + Q]));
         }
 #pragma unroll
       for (int c = 0; c < 3; ++c) RegFft<Q, false>::run(Z[c]);
@@ -220,8 +223,8 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
         float2 sacc[Q];
 #pragma unroll
         for (int n = 0; n < Q; ++n) {
-          const float2 lo = cmul(Z[c][n], cconj(__ldg(&twz[(r * n) % P])));        // term n
-          const float2 hi = cmul(Z[c][n], cconj(__ldg(&twz[(r * (n + Q)) % P])));  // term n + Q
+          const float2 lo = cmul(Z[c][n], cconj(wz[n]));      // term n
+          const float2 hi = cmul(Z[c][n], cconj(wz[n + Q]));  // term n + Q
           const float2 keep = (r >> 1) ? hi : lo;
           const float2 give = (r >> 1) ? lo : hi;
           float2 o;
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
     __syncthreads();
     for (int l0 = 0; l0 < nlines; l0 += NT / S) {
       const int l = l0 + tid / S;
-      line_fft<E, S, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twH);
+      line_fft<E, S, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
     }
     __syncthreads();
     for (int e = tid; e < nlines * ny; e += NT) {
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
 // ---------------------------------------------------------------------------
 template <int E, int S> static size_t xk_smem() { return sizeof(float2) * 3 * kRows * (LineFft<E, S>::kPitch + 1); }
 template <int E, int S> static size_t yzh_smem(int nz) {
-  return sizeof(float2) * (3 * nz + 1) * LineFft<E, S>::kPitch;
+  return sizeof(float2) * ((3 * nz + 1) * LineFft<E, S>::kPitch + E * S + 64);
 }
 
 template <int E, int S>

@@ -80,7 +80,7 @@ template <int E, int S> struct LineFft {
 
 // In-place FFT of `line` (natural order in and out).  `s` in [0, S); the S
 // threads of a line are consecutive lanes of one warp.  twL[q] = W_L^q.
-template <int E, int S, bool INV>
+template <int E, int S, bool INV, bool TW_SHARED = false>
 __device__ __forceinline__ void line_fft(float2* line, int s, const float2* __restrict__ twL) {
   static_assert(E >= S && (E % S) == 0 && S <= 32, "line_fft shape");
   float2 v[E];
@@ -94,7 +94,7 @@ __device__ __forceinline__ void line_fft(float2* line, int s, const float2* __re
   }
 #pragma unroll
   for (int k = 1; k < E; ++k) {
-    float2 w = __ldg(&twL[s * k]);
+    float2 w = TW_SHARED ? twL[s * k] : __ldg(&twL[s * k]);
     if (INV) w.y = -w.y;
     v[k] = cmul(v[k], w);
   }
