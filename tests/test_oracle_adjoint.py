@@ -1,0 +1,52 @@
+"""Pins for the oracle's discrete adjoint: central finite differences of the
+oracle's own forward map (CPU only)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint as adj
+from oracle import micromag as mm
+
+
+@pytest.fixture(scope="module")
+def setup():
+    rng = np.random.default_rng(21)
+    shape = (1, 8, 10)
+    Ms = rng.uniform(6e5, 1e6, size=shape)
+    p = mm.Problem(10, 8, 1, 2e-9, 2e-9, 2e-9, Ms=Ms, A=1.3e-11, D=2e-3, dmi=True, alpha=0.3,
+                   h_bias=(0.0, 0.0, 1e5), Ku=2e4, ku_axis=(0.2, 0.1, 1.0))
+    m0 = rng.normal(size=shape + (3,)) * 1.3
+    obj = lambda m: adj.patch_mean_mz(m, ((2, 6), (3, 7)))  # noqa: E731
+    J, g_m, g_ms = adj.gradient(p, m0, 2e-14, 12, obj)
+    return p, m0, obj, J, g_m, g_ms, rng
+
+
+def test_gradient_wrt_m0_matches_central_differences(setup):
+    p, m0, obj, J, g_m, g_ms, rng = setup
+    for _ in range(3):
+        d = rng.normal(size=m0.shape)
+        fd = adj.central_fd(p, m0, 2e-14, 12, obj, direction_m=d, h=1e-6)
+        an = float((g_m * torch.from_numpy(d)).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-12, (fd, an)
+    # single entries
+    for idx in [(0, 4, 5, 2), (0, 0, 0, 0), (0, 7, 9, 1)]:
+        d = np.zeros(m0.shape)
+        d[idx] = 1.0
+        fd = adj.central_fd(p, m0, 2e-14, 12, obj, direction_m=d, h=1e-6)
+        assert abs(fd - float(g_m[idx])) <= 1e-5 * float(g_m.abs().max()), (idx, fd, float(g_m[idx]))
+
+
+def test_gradient_wrt_ms_matches_central_differences(setup):
+    p, m0, obj, J, g_m, g_ms, rng = setup
+    for _ in range(2):
+        d = rng.normal(size=(1, 8, 10)) * 1e3
+        fd = adj.central_fd(p, m0, 2e-14, 12, obj, direction_ms=d, h=1e-2)
+        an = float((g_ms * torch.from_numpy(d)).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-14, (fd, an)
+
+
+def test_gradient_is_tangent_to_the_initial_normalisation(setup):
+    """J depends on m0 only through m0/|m0|, so dJ/dm0 is orthogonal to m0 in every cell."""
+    p, m0, obj, J, g_m, g_ms, rng = setup
+    dots = (g_m * torch.from_numpy(m0)).sum(-1)
+    assert float(dots.abs().max()) <= 1e-12 * float(g_m.abs().max()) * np.abs(m0).max()
