@@ -196,6 +196,37 @@ mx_status mx_profile_step(mx_ctx *ctx, float *m, int nsteps, double dt, int meth
                           int max_kernels, int *n_kernels);
 const char *mx_kernel_name(int q);
 
+/* ---------------------------------------------------------------------------
+ * Discrete adjoint (gradient of an objective J(m_T) of the final field of an
+ * RK4 run with respect to the raw initial field and the per-cell Ms).  The
+ * gradient is that of the discrete map this library computes: m_0 =
+ * normalize(m0_raw), m_{s+1} = RK4 step of m_s with every stage renormalised.
+ * Usage: mx_adjoint_reserve once, mx_rk_forward_record, then mx_rk_backward
+ * with dJ/dm_T.  The demag term enters through the self-adjoint tensor
+ * convolution; exchange, DMI (with its chiral boundary) and anisotropy through
+ * their Ms-weighted symmetric stencils.
+ * ------------------------------------------------------------------------- */
+
+/* Allocate the adjoint workspaces for runs of `nsteps` RK4 steps keeping a
+ * checkpoint every `checkpoint_every` steps: about
+ * (nsteps/checkpoint_every + checkpoint_every + 16) * nx*ny*nz * 16 bytes.
+ * Replaces any earlier reservation. */
+mx_status mx_adjoint_reserve(mx_ctx *ctx, int nsteps, int checkpoint_every);
+
+/* Forward run for the adjoint: m_final (DEVICE float4) = the field after
+ * nsteps RK4 steps of size dt from normalize(m0_raw) (m0_raw DEVICE float4,
+ * not modified), keeping the checkpoints the backward run needs.  Direct
+ * launches on `stream` (no graph). */
+mx_status mx_rk_forward_record(mx_ctx *ctx, const float *m0_raw, float *m_final, double dt,
+                               mx_stream_t stream);
+
+/* Reverse run for the last mx_rk_forward_record: lam_final = dJ/dm_T (DEVICE
+ * float4; w ignored); grad_m0 (DEVICE float4) receives dJ/dm0_raw; grad_ms
+ * (DEVICE, nx*ny*nz floats, may be NULL) receives dJ/dMs per cell.  Each step
+ * is recomputed from its segment's checkpoint.  Enqueued on `stream`. */
+mx_status mx_rk_backward(mx_ctx *ctx, const float *lam_final, float *grad_m0, float *grad_ms,
+                         mx_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,7 +66,7 @@ def gradient(p, m0_raw, dt, nsteps, objective):
     raw = m0_raw.clone().requires_grad_(True)
     m0 = mm.normalize(raw)
     g_raw, = torch.autograd.grad(m0, raw, grad_outputs=lam)
-    return float(J), g_raw.detach(), g_ms.detach()
+    return float(J.detach()), g_raw.detach(), g_ms.detach()
 
 
 def objective_value(p, m0_raw, dt, nsteps, objective, Ms=None):

@@ -63,6 +63,9 @@ SIGNATURES = {
     "mx_profile_step": (_I, [_P, _P, _I, _D, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_I), _I,
                              ctypes.POINTER(_I)]),
     "mx_kernel_name": (ctypes.c_char_p, [_I]),
+    "mx_adjoint_reserve": (_I, [_P, _I, _I]),
+    "mx_rk_forward_record": (_I, [_P, _P, _P, _D, _P]),
+    "mx_rk_backward": (_I, [_P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -174,3 +177,15 @@ def mx_profile_step(ctx, m, nsteps, dt, method=MX_RK4, stream=None, max_kernels=
     check(lib().mx_profile_step(ctx, ptr(m), int(nsteps), float(dt), int(method), stream_handle(stream),
                                 ms, cnt, max_kernels, ctypes.byref(n)))
     return {lib().mx_kernel_name(q).decode(): (ms[q], cnt[q]) for q in range(n.value) if cnt[q] > 0}
+
+
+def mx_adjoint_reserve(ctx, nsteps, checkpoint_every):
+    check(lib().mx_adjoint_reserve(ctx, int(nsteps), int(checkpoint_every)))
+
+
+def mx_rk_forward_record(ctx, m0_raw, m_final, dt, stream=None):
+    check(lib().mx_rk_forward_record(ctx, ptr(m0_raw), ptr(m_final), float(dt), stream_handle(stream)))
+
+
+def mx_rk_backward(ctx, lam_final, grad_m0, grad_ms=None, stream=None):
+    check(lib().mx_rk_backward(ctx, ptr(lam_final), ptr(grad_m0), ptr(grad_ms), stream_handle(stream)))

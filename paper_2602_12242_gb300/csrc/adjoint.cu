@@ -1,0 +1,320 @@
+// Discrete adjoint of the RK4 step (gradient of an objective of the final
+// magnetisation with respect to the raw initial field and the per-cell Ms).
+//
+// One RK4 step (every stage input renormalised, Sec. II-B):
+//   k1 = f(m0); u1 = m0 + dt/2 k1; m1 = N(u1); k2 = f(m1); u2 = m0 + dt/2 k2;
+//   m2 = N(u2); k3 = f(m2); u3 = m0 + dt k3; m3 = N(u3); k4 = f(m3);
+//   u4 = m0 + dt/6 (k1 + 2 k2 + 2 k3 + k4); m_new = N(u4),
+// with N(u) = u/|u| and f(m) = c [m x H + alpha m x (m x H)] (Eq. 1),
+// c = -gamma0/(1+alpha^2), H = L m + h_bias.  L (demag, exchange, DMI with the
+// chiral ghosts, anisotropy) is linear and Ms-weighted symmetric, so
+// L^T g = Ms (L (g / Ms)).  Reverse sweep for a cotangent lam of m_new:
+//   lam_u4 = J_N(u4)^T lam; lam_m0 = lam_u4; lam_k4 = dt/6 lam_u4;
+//   stage s = 3, 2, 1: lam_ms = f'(m_s)^T lam_ks, lam_us = J_N(u_s)^T lam_ms,
+//     lam_m0 += lam_us, lam_k(s) = (dt/3 or dt/6) lam_u4 + (dt or dt/2) lam_us;
+//   stage 0: lam_m0 += f'(m0)^T lam_k1.
+// J_N(u)^T l = (l - n (n.l)) / |u| with n = N(u); |u| travels in the w slot of
+// every renormalised stage output.  For a stage with state m and cotangent v:
+//   g_m = c [H x v + alpha (v (m.H) + H (v.m) - 2 m (v.H))]
+//   g_H = c [v x m + alpha (m (v.m) - v |m|^2)]
+//   f'(m)^T v = g_m + Ms (L (g_H / Ms))
+//   dJ/dMs_i += m_i . (demag field of g_H)_i - (g_H/Ms)_i . (L_local m)_i
+// (the demag field of M = Ms (g_H/Ms) is what the convolution returns for
+// input g_H / Ms).  The forward keeps a checkpoint every C steps; the reverse
+// sweep recomputes each segment's states and each step's stage states.
+#include <string>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "local.cuh"
+
+namespace mx {
+
+struct AdjWork {
+  int nsteps = 0, every = 0, nckpt = 0;
+  float4* ckpt = nullptr;   // nckpt states
+  float4* seg = nullptr;    // every + 1 states
+  float4* st = nullptr;     // 3 stage states m1, m2, m3
+  float4* hd4 = nullptr;    // demag fields of m0, m1, m2, m3
+  float4* raw = nullptr;    // raw initial field
+  float4* lam_acc = nullptr;
+  float4* lam_u4 = nullptr;
+  float4* lam_k = nullptr;
+  float4* wbuf = nullptr;   // g_H / Ms
+  float4* gm = nullptr;     // g_m
+  float4* hdw = nullptr;    // demag field of wbuf
+  double* dms = nullptr;
+  bool recorded = false;
+  double dt = 0.0;
+};
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+template <bool DMI>
+__global__ void __launch_bounds__(256) adj_prep_kernel(const float4* __restrict__ m, const float4* __restrict__ hd,
+                                                       const float4* __restrict__ lam_k, Grid g, LocalCoef c,
+                                                       float4* __restrict__ wbuf, float4* __restrict__ gm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  const float3 mc = f3(m[idx]);
+  const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
+  Terms t;
+  local_terms<DMI>(m, hd, g, c, i, j, k, idx, mc, 1.f / ms, t);
+  const float3 H = t.demag + t.exch + t.anis + t.dmi + t.zee;
+  const float3 v = f3(lam_k[idx]);
+  const float mH = dot3(mc, H), vm = dot3(v, mc), vH = dot3(v, H), mm = dot3(mc, mc);
+  float3 gmv = c.alpha * (mH * v + vm * H - (2.f * vH) * mc);
+  float3 gh = c.alpha * (vm * mc - mm * v);
+  if (c.precession) {
+    gmv = gmv + cross3(H, v);
+    gh = gh + cross3(v, mc);
+  }
+  gmv = c.llg * gmv;
+  gh = (c.llg / ms) * gh;
+  gm[idx] = make_float4(gmv.x, gmv.y, gmv.z, 0.f);
+  wbuf[idx] = make_float4(gh.x, gh.y, gh.z, 0.f);
+}
+
+// STAGE 3, 2, 1: renormalised stage input; STAGE 0: the step's start state.
+template <bool DMI, int STAGE>
+__global__ void __launch_bounds__(256) adj_finish_kernel(const float4* __restrict__ m, const float4* __restrict__ wbuf,
+                                                         const float4* __restrict__ hdw,
+                                                         const float4* __restrict__ gm,
+                                                         const float4* __restrict__ lam_u4,
+                                                         float4* __restrict__ lam_acc, float4* __restrict__ lam_k,
+                                                         double* __restrict__ dms, Grid g, LocalCoef c, float dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
+  const float inv_ms = 1.f / ms;
+  // L applied to w = g_H / Ms: demag from the convolution, local terms here
+  LocalCoef cl = c;
+  cl.hx = cl.hy = cl.hz = 0.f;  // the bias is not part of the linear operator
+  const float3 wc = f3(wbuf[idx]);
+  Terms tw;
+  local_terms<DMI>(wbuf, hdw, g, cl, i, j, k, idx, wc, inv_ms, tw);
+  const float3 Lw = tw.demag + tw.exch + tw.anis + tw.dmi;
+  const float4 m4 = m[idx];
+  const float3 mc = f3(m4);
+  const float3 lam_m = f3(gm[idx]) + ms * Lw;
+  // Ms gradient: m . (demag of g_H) - w . (L_local m)
+  if (dms) {
+    Terms tm;
+    local_terms<DMI>(m, nullptr, g, cl, i, j, k, idx, mc, inv_ms, tm);
+    const float3 Lm = tm.exch + tm.anis + tm.dmi;
+    dms[idx] += (double)dot3(mc, tw.demag) - (double)dot3(wc, Lm);
+  }
+  if (STAGE == 0) {
+    const float4 a = lam_acc[idx];
+    lam_acc[idx] = make_float4(a.x + lam_m.x, a.y + lam_m.y, a.z + lam_m.z, 0.f);
+  } else {
+    // J_N(u_s)^T lam_m with n = m (unit), |u_s| in m.w
+    const float3 lu = (1.f / m4.w) * (lam_m - dot3(mc, lam_m) * mc);
+    const float4 a = lam_acc[idx];
+    lam_acc[idx] = make_float4(a.x + lu.x, a.y + lu.y, a.z + lu.z, 0.f);
+    const float3 u4 = f3(lam_u4[idx]);
+    const float cu4 = (STAGE == 1) ? dt / 6.f : dt / 3.f;
+    const float cus = (STAGE == 3) ? dt : 0.5f * dt;
+    const float3 nk = cu4 * u4 + cus * lu;
+    lam_k[idx] = make_float4(nk.x, nk.y, nk.z, 0.f);
+  }
+}
+
+// lam_u4 = J_N(u4)^T lam (m_new carries |u4| in w); lam_acc = lam_u4; lam_k = dt/6 lam_u4
+__global__ void adj_begin_kernel(const float4* __restrict__ mnew, float4* __restrict__ lam_acc,
+                                 float4* __restrict__ lam_u4, float4* __restrict__ lam_k, long n, float dt) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const float4 m4 = mnew[idx];
+  const float3 mc = f3(m4);
+  const float3 l = f3(lam_acc[idx]);
+  const float3 lu = (1.f / m4.w) * (l - dot3(mc, l) * mc);
+  lam_u4[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+  lam_acc[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+  lam_k[idx] = make_float4(dt / 6.f * lu.x, dt / 6.f * lu.y, dt / 6.f * lu.z, 0.f);
+}
+
+// grad of the raw field: J_N(raw)^T lam; Ms gradient to float
+__global__ void adj_end_kernel(const float4* __restrict__ raw, const float4* __restrict__ lam, float4* __restrict__ g,
+                               const double* __restrict__ dms, float* __restrict__ gms, long n) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  const float3 r = f3(raw[idx]);
+  const float nr = norm3df(r.x, r.y, r.z);
+  const float3 u = (1.f / nr) * r;
+  const float3 l = f3(lam[idx]);
+  const float3 o = (1.f / nr) * (l - dot3(u, l) * u);
+  g[idx] = make_float4(o.x, o.y, o.z, 0.f);
+  if (gms) gms[idx] = (float)dms[idx];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static void adj_dims(const Grid& g, dim3& grid, dim3& block) {
+  block = dim3(32, 8, 1);
+  if (g.nx < 32) block = dim3(g.nx <= 8 ? 8 : (g.nx <= 16 ? 16 : 32), 256 / (g.nx <= 8 ? 8 : (g.nx <= 16 ? 16 : 32)), 1);
+  grid = dim3((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+}
+
+bool adjoint_recorded(const mx_ctx* ctx) { return ctx->adj && ctx->adj->recorded; }
+
+void adjoint_free(mx_ctx* ctx) {
+  AdjWork* w = ctx->adj;
+  if (!w) return;
+  void* ptrs[] = {w->ckpt, w->seg, w->st, w->hd4, w->raw, w->lam_acc, w->lam_u4, w->lam_k, w->wbuf, w->gm, w->hdw,
+                  w->dms};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete w;
+  ctx->adj = nullptr;
+}
+
+mx_status adjoint_reserve(mx_ctx* ctx, int nsteps, int every) {
+  if (nsteps < 1 || every < 1) {
+    set_error("mx_adjoint_reserve: need nsteps >= 1 and checkpoint_every >= 1");
+    return MX_ERR_INVALID_ARG;
+  }
+  adjoint_free(ctx);
+  AdjWork* w = new AdjWork();
+  ctx->adj = w;
+  w->nsteps = nsteps;
+  w->every = every < nsteps ? every : nsteps;
+  w->nckpt = (nsteps + w->every - 1) / w->every;
+  const long nc = ctx->g.ncell;
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  };
+  alloc((void**)&w->ckpt, sizeof(float4) * nc * w->nckpt);
+  alloc((void**)&w->seg, sizeof(float4) * nc * (w->every + 1));
+  alloc((void**)&w->st, sizeof(float4) * nc * 3);
+  alloc((void**)&w->hd4, sizeof(float4) * nc * 4);
+  alloc((void**)&w->raw, sizeof(float4) * nc);
+  alloc((void**)&w->lam_acc, sizeof(float4) * nc);
+  alloc((void**)&w->lam_u4, sizeof(float4) * nc);
+  alloc((void**)&w->lam_k, sizeof(float4) * nc);
+  alloc((void**)&w->wbuf, sizeof(float4) * nc);
+  alloc((void**)&w->gm, sizeof(float4) * nc);
+  alloc((void**)&w->hdw, sizeof(float4) * nc);
+  alloc((void**)&w->dms, sizeof(double) * nc);
+  if (!ok) {
+    adjoint_free(ctx);
+    set_error("mx_adjoint_reserve: device allocation failed");
+    return MX_ERR_OOM;
+  }
+  return MX_OK;
+}
+
+mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, double dt, cudaStream_t st) {
+  AdjWork* w = ctx->adj;
+  const long nc = ctx->g.ncell;
+  const size_t bytes = sizeof(float4) * nc;
+  MX_CUDA_TRY(cudaMemcpyAsync(w->raw, m0_raw, bytes, cudaMemcpyDeviceToDevice, st));
+  float4* cur = w->seg;  // working state
+  MX_CUDA_TRY(cudaMemcpyAsync(cur, m0_raw, bytes, cudaMemcpyDeviceToDevice, st));
+  MX_TRY(normalize_field(ctx, cur, st));
+  for (int s = 0; s < w->nsteps; ++s) {
+    if (s % w->every == 0)
+      MX_CUDA_TRY(cudaMemcpyAsync(w->ckpt + (long)(s / w->every) * nc, cur, bytes, cudaMemcpyDeviceToDevice, st));
+    MX_TRY(rk4_step_direct(ctx, cur, dt, st));
+  }
+  MX_CUDA_TRY(cudaMemcpyAsync(m_final, cur, bytes, cudaMemcpyDeviceToDevice, st));
+  w->recorded = true;
+  w->dt = dt;
+  return MX_OK;
+}
+
+template <int STAGE>
+static void launch_finish(bool dmi, dim3 grid, dim3 block, cudaStream_t st, AdjWork* w, const float4* m,
+                          const Grid& g, const LocalCoef& c, float dt, bool want_ms) {
+  double* dms = want_ms ? w->dms : nullptr;
+  if (dmi)
+    adj_finish_kernel<true, STAGE><<<grid, block, 0, st>>>(m, w->wbuf, w->hdw, w->gm, w->lam_u4, w->lam_acc,
+                                                           w->lam_k, dms, g, c, dt);
+  else
+    adj_finish_kernel<false, STAGE><<<grid, block, 0, st>>>(m, w->wbuf, w->hdw, w->gm, w->lam_u4, w->lam_acc,
+                                                            w->lam_k, dms, g, c, dt);
+}
+
+mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0, float* grad_ms, cudaStream_t st) {
+  AdjWork* w = ctx->adj;
+  const Grid& g = ctx->g;
+  const long nc = g.ncell;
+  const size_t bytes = sizeof(float4) * nc;
+  const float dt = (float)w->dt;
+  const LocalCoef c = local_coef(ctx);
+  const bool dmi = c.dmi != 0;
+  const bool demag = ctx->p.demag != 0;
+  dim3 grid, block;
+  adj_dims(g, grid, block);
+  const unsigned nb = (unsigned)((nc + 255) / 256);
+  MX_CUDA_TRY(cudaMemcpyAsync(w->lam_acc, lam_final, bytes, cudaMemcpyDeviceToDevice, st));
+  MX_CUDA_TRY(cudaMemsetAsync(w->dms, 0, sizeof(double) * nc, st));
+  if (!demag) {
+    MX_CUDA_TRY(cudaMemsetAsync(w->hd4, 0, 4 * bytes, st));
+    MX_CUDA_TRY(cudaMemsetAsync(w->hdw, 0, bytes, st));
+  }
+  float4* st1 = w->st;
+  float4* st2 = w->st + nc;
+  float4* st3 = w->st + 2 * nc;
+  for (int kseg = w->nckpt - 1; kseg >= 0; --kseg) {
+    const int s0 = kseg * w->every;
+    const int s1 = (s0 + w->every < w->nsteps) ? s0 + w->every : w->nsteps;
+    // states of the segment
+    MX_CUDA_TRY(cudaMemcpyAsync(w->seg, w->ckpt + (long)kseg * nc, bytes, cudaMemcpyDeviceToDevice, st));
+    for (int s = s0; s < s1; ++s) {
+      float4* nxt = w->seg + (long)(s - s0 + 1) * nc;
+      MX_CUDA_TRY(cudaMemcpyAsync(nxt, w->seg + (long)(s - s0) * nc, bytes, cudaMemcpyDeviceToDevice, st));
+      MX_TRY(rk4_step_direct(ctx, nxt, dt, st));
+    }
+    for (int s = s1 - 1; s >= s0; --s) {
+      float4* m = w->seg + (long)(s - s0) * nc;
+      float4* mnew = m + nc;
+      // stage states m1, m2, m3 and the demag field of each stage state
+      const float4* states[4] = {m, st1, st2, st3};
+      float4* outs[3] = {st1, st2, st3};
+      const int modes[3] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2};
+      for (int q = 0; q < 4; ++q) {
+        if (demag) MX_TRY(demag_field(ctx, states[q], w->hd4 + q * nc, st));
+        if (q < 3) {
+          StageIO io{states[q], demag ? w->hd4 + q * nc : nullptr, m, ctx->acc, outs[q], dt, MX_TERM_ALL};
+          MX_TRY(local_stage(ctx, modes[q], io, st));
+        }
+      }
+      adj_begin_kernel<<<nb, 256, 0, st>>>(mnew, w->lam_acc, w->lam_u4, w->lam_k, nc, dt);
+      MX_TRY(launch_check("adj_begin_kernel"));
+      for (int q = 3; q >= 0; --q) {
+        const float4* sm_ = states[q];
+        if (dmi)
+          adj_prep_kernel<true><<<grid, block, 0, st>>>(sm_, w->hd4 + q * nc, w->lam_k, g, c, w->wbuf, w->gm);
+        else
+          adj_prep_kernel<false><<<grid, block, 0, st>>>(sm_, w->hd4 + q * nc, w->lam_k, g, c, w->wbuf, w->gm);
+        MX_TRY(launch_check("adj_prep_kernel"));
+        if (demag) MX_TRY(demag_field(ctx, w->wbuf, w->hdw, st));
+        const bool want_ms = grad_ms != nullptr;
+        switch (q) {
+          case 3: launch_finish<3>(dmi, grid, block, st, w, sm_, g, c, dt, want_ms); break;
+          case 2: launch_finish<2>(dmi, grid, block, st, w, sm_, g, c, dt, want_ms); break;
+          case 1: launch_finish<1>(dmi, grid, block, st, w, sm_, g, c, dt, want_ms); break;
+          default: launch_finish<0>(dmi, grid, block, st, w, sm_, g, c, dt, want_ms); break;
+        }
+        MX_TRY(launch_check("adj_finish_kernel"));
+      }
+    }
+  }
+  adj_end_kernel<<<nb, 256, 0, st>>>(w->raw, w->lam_acc, grad_m0, w->dms, grad_ms, nc);
+  return launch_check("adj_end_kernel");
+}
+
+}  // namespace mx

@@ -127,6 +127,10 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
   return MX_OK;
 }
 
+mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st) {
+  return enqueue_step(ctx, m, dt, MX_RK4, st);
+}
+
 }  // namespace mx
 
 using namespace mx;
@@ -235,6 +239,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
 mx_status mx_destroy(mx_ctx* ctx) {
   if (!ctx) return MX_OK;
   invalidate_graph(ctx);
+  adjoint_free(ctx);
   void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_yh, ctx->tw_y,
                   ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered};
   for (void* q : ptrs)
@@ -510,6 +515,41 @@ mx_status mx_demag_spectrum(mx_ctx* ctx, float* out, mx_stream_t stream) {
   MX_CUDA_TRY(cudaMemcpyAsync(out, ctx->nhat, sizeof(float) * 6 * no, cudaMemcpyDeviceToDevice,
                               (cudaStream_t)stream));
   return MX_OK;
+}
+
+mx_status mx_adjoint_reserve(mx_ctx* ctx, int nsteps, int checkpoint_every) {
+  MX_TRY(check_ctx(ctx));
+  return adjoint_reserve(ctx, nsteps, checkpoint_every);
+}
+
+mx_status mx_rk_forward_record(mx_ctx* ctx, const float* m0_raw, float* m_final, double dt, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(m0_raw, "mx_rk_forward_record: m0_raw"));
+  MX_TRY(check_vec_ptr(m_final, "mx_rk_forward_record: m_final"));
+  if (!ctx->adj) {
+    set_error("mx_rk_forward_record: call mx_adjoint_reserve first");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (!(dt > 0) || !isfinite(dt)) {
+    set_error("mx_rk_forward_record: need finite dt > 0");
+    return MX_ERR_INVALID_ARG;
+  }
+  if (ctx->p.demag && !ctx->built) {
+    set_error("mx_rk_forward_record: demag kernel not built");
+    return MX_ERR_NOT_BUILT;
+  }
+  return adjoint_forward(ctx, (const float4*)m0_raw, (float4*)m_final, dt, (cudaStream_t)stream);
+}
+
+mx_status mx_rk_backward(mx_ctx* ctx, const float* lam_final, float* grad_m0, float* grad_ms, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(lam_final, "mx_rk_backward: lam_final"));
+  MX_TRY(check_vec_ptr(grad_m0, "mx_rk_backward: grad_m0"));
+  if (!adjoint_recorded(ctx)) {
+    set_error("mx_rk_backward: no recorded forward run (mx_rk_forward_record)");
+    return MX_ERR_INVALID_ARG;
+  }
+  return adjoint_backward(ctx, (const float4*)lam_final, (float4*)grad_m0, grad_ms, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -96,6 +96,7 @@ struct LocalCoef {
 };
 
 struct Profiler;
+struct AdjWork;
 
 }  // namespace mx
 
@@ -144,4 +145,7 @@ struct mx_ctx {
 
   // profiling hook (events around each launch when non-null)
   mx::Profiler* prof = nullptr;
+
+  // adjoint workspaces (mx_adjoint_reserve)
+  mx::AdjWork* adj = nullptr;
 };

@@ -46,6 +46,16 @@ mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 // newell.cu
 mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st);
 
+// adjoint.cu
+mx_status adjoint_reserve(mx_ctx* ctx, int nsteps, int every);
+void adjoint_free(mx_ctx* ctx);
+mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, double dt, cudaStream_t st);
+mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0, float* grad_ms, cudaStream_t st);
+bool adjoint_recorded(const mx_ctx* ctx);
+
+// api.cu
+mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st);
+
 // local.cu
 enum LocalMode { LM_HEFF = 0, LM_RHS, LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3, LM_EULER };
 struct StageIO {

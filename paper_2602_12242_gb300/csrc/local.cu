@@ -18,64 +18,9 @@
 //             (renormalisation after every stage, Sec. II-B)
 #include "common.cuh"
 #include "kernels.cuh"
+#include "local.cuh"
 
 namespace mx {
-
-struct Terms {
-  float3 demag, exch, dmi, anis, zee;
-};
-
-__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-
-// All field terms at cell (i, j, k).
-template <bool DMI>
-__device__ __forceinline__ void local_terms(const float4* __restrict__ m, const float4* __restrict__ hd,
-                                            const Grid& g, const LocalCoef& c, int i, int j, int k, long idx,
-                                            float3 mc, float inv_ms, Terms& t) {
-  const long sx = 1, sy = g.nx, sz = (long)g.nx * g.ny;
-  float3 xm, xp, ym, yp, zm, zp;
-  // chiral ghosts (kdx, kdy are zero when DMI is off)
-  xp = (i + 1 < g.nx) ? f3(__ldg(&m[idx + sx])) : make_float3(mc.x - c.kdx * mc.z, mc.y, mc.z + c.kdx * mc.x);
-  xm = (i > 0) ? f3(__ldg(&m[idx - sx])) : make_float3(mc.x + c.kdx * mc.z, mc.y, mc.z - c.kdx * mc.x);
-  yp = (j + 1 < g.ny) ? f3(__ldg(&m[idx + sy])) : make_float3(mc.x, mc.y - c.kdy * mc.z, mc.z + c.kdy * mc.y);
-  ym = (j > 0) ? f3(__ldg(&m[idx - sy])) : make_float3(mc.x, mc.y + c.kdy * mc.z, mc.z - c.kdy * mc.y);
-  zp = (k + 1 < g.nz) ? f3(__ldg(&m[idx + sz])) : mc;
-  zm = (k > 0) ? f3(__ldg(&m[idx - sz])) : mc;
-  const float3 two = 2.f * mc;
-  const float3 lap = c.inv_dx2 * (xp + xm - two) + c.inv_dy2 * (yp + ym - two) + c.inv_dz2 * (zp + zm - two);
-  t.exch = (c.cA * inv_ms) * lap;
-  if (DMI) {
-    const float3 ddx = c.inv_2dx * (xp - xm);
-    const float3 ddy = c.inv_2dy * (yp - ym);
-    t.dmi = (c.cD * inv_ms) * make_float3(ddx.z, ddy.z, -(ddx.x + ddy.y));
-  } else {
-    t.dmi = make_float3(0.f, 0.f, 0.f);
-  }
-  const float3 e = c.axis_map ? f3(__ldg(&c.axis_map[idx])) : make_float3(c.ax, c.ay, c.az);
-  const float cK = c.ku_map ? (__ldg(&c.ku_map[idx]) * (float)(2.0 / kMu0)) : c.cK;
-  t.anis = (cK * inv_ms * dot3(mc, e)) * e;
-  t.zee = make_float3(c.hx, c.hy, c.hz);
-  t.demag = hd ? f3(__ldg(&hd[idx])) : make_float3(0.f, 0.f, 0.f);
-}
-
-__device__ __forceinline__ float3 llg(const LocalCoef& c, float3 mc, float3 H) {
-  const float3 mxH = cross3(mc, H);
-  const float3 mxmxH = cross3(mc, mxH);
-  const float3 p = c.precession ? mxH : make_float3(0.f, 0.f, 0.f);
-  return c.llg * (p + c.alpha * mxmxH);
-}
-
-__device__ __forceinline__ float3 unit(float3 v) {
-  const float r = rnorm3df(v.x, v.y, v.z);
-  return r * v;
-}
 
 template <int MODE, bool DMI>
 __global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoef c, int* flag) {
@@ -90,6 +35,7 @@ __global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoe
   Terms t;
   local_terms<DMI>(io.m, io.hd, g, c, i, j, k, idx, mc, inv_ms, t);
   float3 out;
+  float wout = 0.f;  // |u| of a renormalised stage output (used by the adjoint)
   if (MODE == LM_HEFF) {
     out = make_float3(0.f, 0.f, 0.f);
     if (io.terms & MX_TERM_DEMAG) out = out + t.demag;
@@ -103,23 +49,23 @@ __global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoe
     if (MODE == LM_RHS) {
       out = kk;
     } else if (MODE == LM_EULER) {
-      out = unit(mc + io.dt * kk);
+      out = unit_norm(mc + io.dt * kk, wout);
     } else if (MODE == LM_RK4_S0) {
       io.acc[idx] = make_float4(kk.x, kk.y, kk.z, 0.f);
-      out = unit(mc + (0.5f * io.dt) * kk);
+      out = unit_norm(mc + (0.5f * io.dt) * kk, wout);
     } else {
       const float3 m0 = f3(io.m0[idx]);
       const float3 a = f3(io.acc[idx]);
       if (MODE == LM_RK4_S3) {
-        out = unit(m0 + (io.dt * (1.f / 6.f)) * (a + kk));
+        out = unit_norm(m0 + (io.dt * (1.f / 6.f)) * (a + kk), wout);
       } else {
         io.acc[idx] = make_float4(a.x + 2.f * kk.x, a.y + 2.f * kk.y, a.z + 2.f * kk.z, 0.f);
-        out = unit(m0 + ((MODE == LM_RK4_S1 ? 0.5f : 1.f) * io.dt) * kk);
+        out = unit_norm(m0 + ((MODE == LM_RK4_S1 ? 0.5f : 1.f) * io.dt) * kk, wout);
       }
     }
   }
   if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, 1);
-  io.out[idx] = make_float4(out.x, out.y, out.z, 0.f);
+  io.out[idx] = make_float4(out.x, out.y, out.z, wout);
 }
 
 __global__ void normalize_kernel(float4* m, long n, int* flag) {

@@ -153,3 +153,21 @@ class Context:
     def profile_step(self, m, nsteps, dt, method="rk4", stream=None):
         self._check(m)
         return L.mx_profile_step(self.h, m, nsteps, dt, L.MX_RK4 if method == "rk4" else L.MX_EULER, stream)
+
+    # -- adjoint ---------------------------------------------------------------
+    def adjoint_reserve(self, nsteps, checkpoint_every):
+        L.mx_adjoint_reserve(self.h, nsteps, checkpoint_every)
+        self._adj = (int(nsteps), int(checkpoint_every))
+
+    def rk_forward_record(self, m0_raw, dt, stream=None):
+        self._check(m0_raw)
+        out = torch.empty_like(m0_raw)
+        L.mx_rk_forward_record(self.h, m0_raw, out, dt, stream)
+        return out
+
+    def rk_backward(self, lam_final, want_ms=True, stream=None):
+        self._check(lam_final)
+        g = torch.empty_like(lam_final)
+        gms = torch.empty(self.shape, dtype=torch.float32, device=lam_final.device) if want_ms else None
+        L.mx_rk_backward(self.h, lam_final.contiguous(), g, gms, stream)
+        return g, gms

@@ -1,0 +1,108 @@
+"""GPU discrete adjoint (mx_rk_forward_record / mx_rk_backward) vs the FP64
+oracle's discrete adjoint and central finite differences.
+
+Tolerance: 1e-3 relative (L2 over the whole gradient field, and per sampled
+direction) -- the stated gradient tolerance for the FP32 path.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import cfg_of, context, problem, rel_l2, t64
+from oracle import adjoint as oadj
+from oracle import micromag as mm
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 1e-3
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def dev4(a):
+    from paper_2602_12242_gb300.solver import to_dev4
+    return to_dev4(a)
+
+
+def run_case(c, Ms, m0_raw, nsteps, every, patch, dt):
+    ctx = context(c, Ms=Ms)
+    ctx.adjoint_reserve(nsteps, every)
+    mT = ctx.rk_forward_record(dev4(m0_raw), dt)
+    lam = torch.zeros_like(mT)
+    (y0, y1), (x0, x1) = patch
+    lam[:, y0:y1, x0:x1, 2] = 1.0 / ((y1 - y0) * (x1 - x0) * c["nz"])
+    g, gms = ctx.rk_backward(lam)
+    torch.cuda.synchronize()
+    return ctx, mT, g[..., :3].double().cpu().numpy(), gms.double().cpu().numpy()
+
+
+def test_adjoint_matches_oracle_discrete_adjoint():
+    rng = np.random.default_rng(31)
+    c = cfg_of(nx=24, ny=20, nz=1, D=2e-3, dmi=True, Ku=0.0, alpha=0.3, h_bias=(0.0, 0.0, 1e5))
+    shape = (1, 20, 24)
+    Ms = f32(rng.uniform(6e5, 1e6, size=shape))
+    m0 = f32(rng.normal(size=shape + (3,)))
+    patch = ((6, 14), (8, 16))
+    dt, nsteps = 2e-14, 30
+    ctx, mT, g, gms = run_case(c, Ms, m0, nsteps, 7, patch, dt)
+    p = problem(c, Ms=Ms)
+    J, g_ref, gms_ref = oadj.gradient(p, m0, dt, nsteps, lambda m: oadj.patch_mean_mz(m, patch))
+    assert rel_l2(g, g_ref.numpy()) <= TOL_GRAD, rel_l2(g, g_ref.numpy())
+    assert rel_l2(gms, gms_ref.numpy()) <= TOL_GRAD, rel_l2(gms, gms_ref.numpy())
+    # the recorded forward equals the oracle's trajectory
+    ref_T = oadj.forward_states(p, m0, dt, nsteps)[-1].numpy()
+    assert np.abs(mT[..., :3].double().cpu().numpy() - ref_T).max() <= 1e-4
+
+
+def test_adjoint_with_demag_off_and_anisotropy():
+    rng = np.random.default_rng(32)
+    c = cfg_of(nx=16, ny=12, nz=3, Ku=3e4, ku_axis=(0.3, -0.2, 1.0), alpha=0.2, h_bias=(2e4, 0.0, 5e4))
+    shape = (3, 12, 16)
+    Ms = f32(rng.uniform(6e5, 1e6, size=shape))
+    m0 = f32(rng.normal(size=shape + (3,)))
+    patch = ((2, 9), (3, 11))
+    ctx = context(c, Ms=Ms, demag=False)
+    ctx.adjoint_reserve(12, 5)
+    mT = ctx.rk_forward_record(dev4(m0), 1e-14)
+    lam = torch.zeros_like(mT)
+    lam[:, 2:9, 3:11, 2] = 1.0 / (7 * 8 * 3)
+    g, gms = ctx.rk_backward(lam)
+    p = problem(c, Ms=Ms, demag=False)
+    J, g_ref, gms_ref = oadj.gradient(p, m0, 1e-14, 12, lambda m: oadj.patch_mean_mz(m, patch))
+    assert rel_l2(g[..., :3].double().cpu().numpy(), g_ref.numpy()) <= TOL_GRAD
+    assert rel_l2(gms.double().cpu().numpy(), gms_ref.numpy()) <= TOL_GRAD
+
+
+def test_autograd_function_routes_both_gradients():
+    from paper_2602_12242_gb300.autograd import rk4_run
+    rng = np.random.default_rng(33)
+    c = cfg_of(nx=20, ny=16, nz=1, D=1.5e-3, dmi=True, Ku=0.0, alpha=0.3, h_bias=(0.0, 0.0, 1e5))
+    shape = (1, 16, 20)
+    Ms = f32(rng.uniform(6e5, 1e6, size=shape))
+    m0 = f32(rng.normal(size=shape + (3,)))
+    ctx = context(c, Ms=Ms)
+    ctx.adjoint_reserve(10, 4)
+    m0_t = dev4(m0).requires_grad_(True)
+    ms_t = torch.as_tensor(Ms, dtype=torch.float32, device="cuda").requires_grad_(True)
+    mT = rk4_run(ctx, m0_t, 2e-14, ms_map=ms_t)
+    J = mT[:, 4:12, 5:15, 2].mean()
+    J.backward()
+    p = problem(c, Ms=Ms)
+    Jr, g_ref, gms_ref = oadj.gradient(p, m0, 2e-14, 10, lambda m: oadj.patch_mean_mz(m, ((4, 12), (5, 15))))
+    assert abs(float(J) - Jr) <= 1e-5
+    assert rel_l2(m0_t.grad[..., :3].double().cpu().numpy(), g_ref.numpy()) <= TOL_GRAD
+    assert rel_l2(ms_t.grad.double().cpu().numpy(), gms_ref.numpy()) <= TOL_GRAD
+
+
+def test_adjoint_errors():
+    from paper_2602_12242_gb300 import MxError, _lib
+    c = cfg_of(nx=8, ny=8, nz=1)
+    ctx = context(c)
+    lam = dev4(np.zeros((1, 8, 8, 3)))
+    with pytest.raises(MxError) as ei:
+        ctx.rk_backward(lam)
+    assert ei.value.status == _lib.MX_ERR_INVALID_ARG
+    with pytest.raises(MxError):
+        ctx.adjoint_reserve(0, 1)
