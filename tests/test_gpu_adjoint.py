@@ -91,7 +91,7 @@ def test_autograd_function_routes_both_gradients():
     J.backward()
     p = problem(c, Ms=Ms)
     Jr, g_ref, gms_ref = oadj.gradient(p, m0, 2e-14, 10, lambda m: oadj.patch_mean_mz(m, ((4, 12), (5, 15))))
-    assert abs(float(J) - Jr) <= 1e-5
+    assert abs(float(J.detach()) - Jr) <= 1e-5
     assert rel_l2(m0_t.grad[..., :3].double().cpu().numpy(), g_ref.numpy()) <= TOL_GRAD
     assert rel_l2(ms_t.grad.double().cpu().numpy(), gms_ref.numpy()) <= TOL_GRAD
 
@@ -106,3 +106,53 @@ def test_adjoint_errors():
     assert ei.value.status == _lib.MX_ERR_INVALID_ARG
     with pytest.raises(MxError):
         ctx.adjoint_reserve(0, 1)
+
+
+def _workload(nsteps, every):
+    from paper_2602_12242_gb300 import inputs
+    c = dict(inputs.CONFIGS["adjoint"])
+    Ms, _, _ = inputs.material("adjoint")
+    Ms = f32(Ms)
+    m0 = f32(inputs.initial_m("adjoint"))
+    patch = ((48, 80), (48, 80))  # central 32 x 32 of 128 x 128
+    ctx, mT, g, gms = run_case(c, Ms, m0, nsteps, every, patch, c["dt"])
+    return c, Ms, m0, patch, g, gms
+
+
+def _check_against_oracle(c, Ms, m0, patch, g, gms, nsteps, ndirs):
+    p = problem(c, Ms=Ms)
+    obj = lambda m: oadj.patch_mean_mz(m, patch)  # noqa: E731
+    J, g_ref, gms_ref = oadj.gradient(p, m0, c["dt"], nsteps, obj)
+    assert rel_l2(g, g_ref.numpy()) <= TOL_GRAD, rel_l2(g, g_ref.numpy())
+    assert rel_l2(gms, gms_ref.numpy()) <= TOL_GRAD, rel_l2(gms, gms_ref.numpy())
+    # central differences (h = 1e-4) along unit-norm random directions of (m0, Ms/1e6)
+    # and along single entries inside the objective's patch
+    rng = np.random.default_rng(34)
+    dirs = []
+    for _ in range(ndirs):
+        dm = rng.normal(size=m0.shape)
+        ds = rng.normal(size=Ms.shape)
+        nrm = np.sqrt((dm ** 2).sum() + (ds ** 2).sum())
+        dirs.append((dm / nrm, 1e6 * ds / nrm))
+    for idx in [(0, 60, 61, 2), (0, 70, 55, 0)]:
+        dm = np.zeros(m0.shape)
+        dm[idx] = 1.0
+        dirs.append((dm, None))
+    for dm, ds in dirs:
+        fd = oadj.central_fd(p, m0, c["dt"], nsteps, obj, direction_m=dm, direction_ms=ds, h=1e-4)
+        an = float((g * dm).sum() + (0.0 if ds is None else (gms * ds).sum()))
+        assert abs(an - fd) <= TOL_GRAD * abs(fd), (an, fd)
+
+
+def test_adjoint_workload_grid_200_steps():
+    """The adjoint workload's grid and material (128x128x1, Ms map in [6e5, 1e6], DMI,
+    bias 1e5 A/m along z), 200 RK4 steps with a checkpoint every 20."""
+    c, Ms, m0, patch, g, gms = _workload(200, 20)
+    _check_against_oracle(c, Ms, m0, patch, g, gms, 200, 1)
+
+
+@pytest.mark.slow
+def test_adjoint_workload_full_2000_steps():
+    """The full adjoint workload: 2000 RK4 steps, a checkpoint every 100."""
+    c, Ms, m0, patch, g, gms = _workload(2000, 100)
+    _check_against_oracle(c, Ms, m0, patch, g, gms, 2000, 2)
