@@ -168,6 +168,34 @@ mx_status mx_rk_step(mx_ctx *ctx, float *m, int nsteps, double dt, int method,
  * FP64.  e_out is a HOST array.  Synchronises `stream`. */
 mx_status mx_energy(mx_ctx *ctx, const float *m, double e_out[5], mx_stream_t stream);
 
+/* Energies [J] like mx_energy, for callers that cannot allocate device
+ * memory -- code that runs inside a device-memory budget owned by another
+ * framework, or a latency-critical loop where an allocation's implicit
+ * synchronisation would stall other work.  The paper has no counterpart; this
+ * is a property of the library, not of the method.
+ * No context, no cudaMalloc/cudaFree or allocating library call: the caller
+ * passes every input and the output, and the only scratch (five FP64 partial
+ * sums per 256-cell block) lives in a fixed-size array inside the library that
+ * every GPU which loads the library holds until the process exits (640 KiB).
+ *   p        HOST parameters (grid, cell, material; demag fields unused)
+ *   m        DEVICE float4 field, nx*ny*nz records
+ *   h_demag  DEVICE float4 demag field of m (e.g. from mx_heff with
+ *            MX_TERM_DEMAG), or NULL: demag energy 0
+ *   ms_map, ku_map  DEVICE nx*ny*nz floats or NULL (scalars of p)
+ *   axis_map DEVICE float4 unit axes or NULL (p->ku_axis)
+ *   e_out    DEVICE array of 5 doubles: demag, exchange, anisotropy, DMI,
+ *            Zeeman, as in mx_energy
+ * Limit: nx*ny*nz <= 4,194,304 cells; larger grids return MX_ERR_UNSUPPORTED.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Enqueued on `stream`, no synchronisation.
+ * Every call shares the one array, which keeps the last call's contents (each
+ * call overwrites every row it reads), so calls that overlap on the GPU race:
+ * order them on one stream or synchronise between them. */
+mx_status mx_energy_noalloc(const mx_params *p, const float *m, const float *h_demag,
+                            const float *ms_map, const float *ku_map, const float *axis_map,
+                            double *e_out, mx_stream_t stream);
+
 /* Synchronise `stream`; return MX_ERR_NONFINITE (and clear the flag) if any
  * kernel of this context produced a NaN or Inf since the last mx_sync. */
 mx_status mx_sync(mx_ctx *ctx, mx_stream_t stream);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "mx_profile_step": (_I, [_P, _P, _I, _D, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_I), _I,
                              ctypes.POINTER(_I)]),
     "mx_kernel_name": (ctypes.c_char_p, [_I]),
+    "mx_energy_noalloc": (_I, [ctypes.POINTER(mx_params), _P, _P, _P, _P, _P, _P, _P]),
     "mx_adjoint_reserve": (_I, [_P, _I, _I]),
     "mx_rk_forward_record": (_I, [_P, _P, _P, _D, _P]),
     "mx_rk_backward": (_I, [_P, _P, _P, _P, _P]),
@@ -189,3 +190,10 @@ def mx_rk_forward_record(ctx, m0_raw, m_final, dt, stream=None):
 
 def mx_rk_backward(ctx, lam_final, grad_m0, grad_ms=None, stream=None):
     check(lib().mx_rk_backward(ctx, ptr(lam_final), ptr(grad_m0), ptr(grad_ms), stream_handle(stream)))
+
+
+def mx_energy_noalloc(params, m, e_out, h_demag=None, ms_map=None, ku_map=None, axis_map=None, stream=None):
+    """Energies into the caller's DEVICE buffer e_out (5 float64) without any
+    device allocation inside the library (see include/mx.h)."""
+    check(lib().mx_energy_noalloc(ctypes.byref(params), ptr(m), ptr(h_demag), ptr(ms_map), ptr(ku_map),
+                                  ptr(axis_map), ptr(e_out), stream_handle(stream)))
