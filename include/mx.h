@@ -225,6 +225,63 @@ mx_status mx_profile_step(mx_ctx *ctx, float *m, int nsteps, double dt, int meth
 const char *mx_kernel_name(int q);
 
 /* ---------------------------------------------------------------------------
+ * Learned demag surrogate (the paper's ML module, Sec. II-D: a network trained
+ * offline on (M, H_demag) pairs from the FFT solver replaces the demag term
+ * with no change to the integration).  Here: a 3D conv net 3 -> 32 -> 64 ->
+ * 32 -> 3 channels, 3x3x3 kernels, zero padding 1, exact GELU after the first
+ * three layers; BF16 activations, FP32 master weights, tensor-core implicit
+ * GEMM.  Inputs m are normalised per component (mean/std), outputs are the
+ * normalised demag field (Gaussian normaliser, Sec. II-D).  Training: SmoothL1
+ * loss (beta 1, mean over cells, components and batch) and Adam
+ * (beta 0.9/0.999, eps 1e-8) with L2-coupled weight decay.
+ * Parameter vector (FP32, DEVICE): W1 (32x3x3x3x3), b1 (32), W2 (64x32x27),
+ * b2 (64), W3 (32x64x27), b3 (32), W4 (3x32x27), b4 (3); W[co][ci][dz][dy][dx]
+ * multiplies input cell (z+dz-1, y+dy-1, x+dx-1).
+ * ------------------------------------------------------------------------- */
+typedef struct mx_cnn mx_cnn;
+
+/* Number of parameters (115,907). */
+int mx_cnn_num_params(void);
+
+/* Network for fields of nx*ny*nz cells and batches up to max_batch;
+ * allocates all of its buffers (about 13 MB per sample of 64x64x4).  The
+ * parameters start at zero. */
+mx_status mx_cnn_create(mx_cnn **out, int nx, int ny, int nz, int max_batch);
+mx_status mx_cnn_destroy(mx_cnn *net);
+
+/* Copy the parameter vector in (resets the Adam moments) / out. */
+mx_status mx_cnn_set_params(mx_cnn *net, const float *params, mx_stream_t stream);
+mx_status mx_cnn_get_params(const mx_cnn *net, float *params, mx_stream_t stream);
+
+/* Normaliser, host array: input mean[3], input std[3], output mean[3],
+ * output std[3] (std > 0). */
+mx_status mx_cnn_set_normalizer(mx_cnn *net, const double stats[12]);
+
+/* h = network(m) for `batch` fields stored back to back (DEVICE float4
+ * arrays of batch*nx*ny*nz records). */
+mx_status mx_cnn_forward(mx_cnn *net, const float *m, float *h, int batch, mx_stream_t stream);
+
+/* Forward + SmoothL1 loss against h_target (DEVICE float4, raw field; the
+ * normaliser is applied inside) + backward.  The gradient is kept for
+ * mx_cnn_adam_step; loss_out (DEVICE, 1 float) and grad_out (DEVICE,
+ * mx_cnn_num_params floats) receive copies when not NULL. */
+mx_status mx_cnn_loss_grad(mx_cnn *net, const float *m, const float *h_target, int batch,
+                           float *loss_out, float *grad_out, mx_stream_t stream);
+
+/* One Adam step with the last gradient: g += weight_decay * theta, then
+ * the bias-corrected Adam update with learning rate lr. */
+mx_status mx_cnn_adam_step(mx_cnn *net, double lr, double weight_decay, mx_stream_t stream);
+
+/* Use `net` (same grid) for the demag term of every later mx_heff,
+ * mx_llg_rhs, mx_rk_step and mx_energy call of ctx; NULL returns to the FFT
+ * convolution.  The caller keeps `net` alive while it is set. */
+mx_status mx_set_demag_surrogate(mx_ctx *ctx, mx_cnn *net);
+
+/* Relative L2 difference ||a - b|| / ||b|| of two DEVICE float4 fields of
+ * the context's grid (xyz only), in FP64; synchronises `stream`. */
+mx_status mx_rel_l2(mx_ctx *ctx, const float *a, const float *b, double *out, mx_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Discrete adjoint (gradient of an objective J(m_T) of the final field of an
  * RK4 run with respect to the raw initial field and the per-cell Ms).  The
  * gradient is that of the discrete map this library computes: m_0 =

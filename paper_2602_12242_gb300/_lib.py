@@ -64,6 +64,17 @@ SIGNATURES = {
                              ctypes.POINTER(_I)]),
     "mx_kernel_name": (ctypes.c_char_p, [_I]),
     "mx_energy_noalloc": (_I, [ctypes.POINTER(mx_params), _P, _P, _P, _P, _P, _P, _P]),
+    "mx_cnn_num_params": (_I, []),
+    "mx_cnn_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
+    "mx_cnn_destroy": (_I, [_P]),
+    "mx_cnn_set_params": (_I, [_P, _P, _P]),
+    "mx_cnn_get_params": (_I, [_P, _P, _P]),
+    "mx_cnn_set_normalizer": (_I, [_P, ctypes.POINTER(_D)]),
+    "mx_cnn_forward": (_I, [_P, _P, _P, _I, _P]),
+    "mx_cnn_loss_grad": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "mx_cnn_adam_step": (_I, [_P, _D, _D, _P]),
+    "mx_set_demag_surrogate": (_I, [_P, _P]),
+    "mx_rel_l2": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "mx_adjoint_reserve": (_I, [_P, _I, _I]),
     "mx_rk_forward_record": (_I, [_P, _P, _P, _D, _P]),
     "mx_rk_backward": (_I, [_P, _P, _P, _P, _P]),
@@ -197,3 +208,53 @@ def mx_energy_noalloc(params, m, e_out, h_demag=None, ms_map=None, ku_map=None, 
     device allocation inside the library (see include/mx.h)."""
     check(lib().mx_energy_noalloc(ctypes.byref(params), ptr(m), ptr(h_demag), ptr(ms_map), ptr(ku_map),
                                   ptr(axis_map), ptr(e_out), stream_handle(stream)))
+
+
+def mx_cnn_num_params():
+    return int(lib().mx_cnn_num_params())
+
+
+def mx_cnn_create(nx, ny, nz, max_batch):
+    h = ctypes.c_void_p()
+    check(lib().mx_cnn_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(max_batch)))
+    return h
+
+
+def mx_cnn_destroy(net):
+    check(lib().mx_cnn_destroy(net))
+
+
+def mx_cnn_set_params(net, params, stream=None):
+    check(lib().mx_cnn_set_params(net, ptr(params), stream_handle(stream)))
+
+
+def mx_cnn_get_params(net, params, stream=None):
+    check(lib().mx_cnn_get_params(net, ptr(params), stream_handle(stream)))
+
+
+def mx_cnn_set_normalizer(net, stats):
+    arr = (_D * 12)(*[float(v) for v in stats])
+    check(lib().mx_cnn_set_normalizer(net, arr))
+
+
+def mx_cnn_forward(net, m, h, batch, stream=None):
+    check(lib().mx_cnn_forward(net, ptr(m), ptr(h), int(batch), stream_handle(stream)))
+
+
+def mx_cnn_loss_grad(net, m, h_target, batch, loss_out=None, grad_out=None, stream=None):
+    check(lib().mx_cnn_loss_grad(net, ptr(m), ptr(h_target), int(batch), ptr(loss_out), ptr(grad_out),
+                                 stream_handle(stream)))
+
+
+def mx_cnn_adam_step(net, lr, weight_decay, stream=None):
+    check(lib().mx_cnn_adam_step(net, float(lr), float(weight_decay), stream_handle(stream)))
+
+
+def mx_set_demag_surrogate(ctx, net):
+    check(lib().mx_set_demag_surrogate(ctx, net))
+
+
+def mx_rel_l2(ctx, a, b, stream=None):
+    out = _D()
+    check(lib().mx_rel_l2(ctx, ptr(a), ptr(b), ctypes.byref(out), stream_handle(stream)))
+    return out.value

@@ -131,6 +131,26 @@ mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st) {
   return enqueue_step(ctx, m, dt, MX_RK4, st);
 }
 
+// sums of |a - b|^2 and |b|^2 over the xyz of float4 records
+__global__ void rel_l2_kernel(const float4* __restrict__ a, const float4* __restrict__ b, long n,
+                              double* __restrict__ out) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float4 x = a[i], y = b[i];
+    const double dx = (double)x.x - y.x, dy = (double)x.y - y.y, dz = (double)x.z - y.z;
+    s0 += dx * dx + dy * dy + dz * dz;
+    s1 += (double)y.x * y.x + (double)y.y * y.y + (double)y.z * y.z;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], s0);
+    atomicAdd(&out[1], s1);
+  }
+}
+
 }  // namespace mx
 
 using namespace mx;
@@ -202,6 +222,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   alloc((void**)&ctx->acc, sizeof(float4) * nc);
   alloc((void**)&ctx->flag, sizeof(int));
   alloc((void**)&ctx->ered, sizeof(double) * 5);
+  alloc((void**)&ctx->red2, sizeof(double) * 2);
   mx_status st = MX_OK;
   if (ok) st = demag_setup(ctx);
   if (ok && st == MX_OK) st = fast_setup(ctx);
@@ -241,7 +262,7 @@ mx_status mx_destroy(mx_ctx* ctx) {
   invalidate_graph(ctx);
   adjoint_free(ctx);
   void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_yh, ctx->tw_y,
-                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered};
+                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered, ctx->red2};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -340,7 +361,7 @@ mx_status mx_heff(mx_ctx* ctx, const float* m, float* h, int terms, mx_stream_t 
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool demag = (terms & MX_TERM_DEMAG) != 0;
-  if (demag && !ctx->built) {
+  if (demag && !ctx->built && !ctx->surrogate) {
     set_error("mx_heff: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -359,7 +380,7 @@ mx_status mx_llg_rhs(mx_ctx* ctx, const float* m, float* dmdt, mx_stream_t strea
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool demag = ctx->p.demag != 0;
-  if (demag && !ctx->built) {
+  if (demag && !ctx->built && !ctx->surrogate) {
     set_error("mx_llg_rhs: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -375,7 +396,7 @@ static mx_status check_step_args(mx_ctx* ctx, const float* m, int nsteps, double
     set_error("mx_rk_step: need nsteps >= 0, finite dt > 0, method MX_RK4 or MX_EULER");
     return MX_ERR_INVALID_ARG;
   }
-  if (ctx->p.demag && !ctx->built) {
+  if (ctx->p.demag && !ctx->built && !ctx->surrogate) {
     set_error("mx_rk_step: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -458,7 +479,7 @@ mx_status mx_energy(mx_ctx* ctx, const float* m, double e_out[5], mx_stream_t st
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool demag = ctx->p.demag != 0;
-  if (demag && !ctx->built) {
+  if (demag && !ctx->built && !ctx->surrogate) {
     set_error("mx_energy: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -550,6 +571,36 @@ mx_status mx_rk_backward(mx_ctx* ctx, const float* lam_final, float* grad_m0, fl
     return MX_ERR_INVALID_ARG;
   }
   return adjoint_backward(ctx, (const float4*)lam_final, (float4*)grad_m0, grad_ms, (cudaStream_t)stream);
+}
+
+mx_status mx_set_demag_surrogate(mx_ctx* ctx, mx_cnn* net) {
+  MX_TRY(check_ctx(ctx));
+  if (net && !cnn_matches(net, ctx->g)) {
+    set_error("mx_set_demag_surrogate: the network's grid differs from the context's");
+    return MX_ERR_INVALID_ARG;
+  }
+  invalidate_graph(ctx);
+  ctx->surrogate = net;
+  return MX_OK;
+}
+
+mx_status mx_rel_l2(mx_ctx* ctx, const float* a, const float* b, double* out, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(a, "mx_rel_l2: a"));
+  MX_TRY(check_vec_ptr(b, "mx_rel_l2: b"));
+  if (!out) {
+    set_error("mx_rel_l2: NULL out");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  MX_CUDA_TRY(cudaMemsetAsync(ctx->red2, 0, sizeof(double) * 2, st));
+  rel_l2_kernel<<<304, 256, 0, st>>>((const float4*)a, (const float4*)b, ctx->g.ncell, ctx->red2);
+  MX_TRY(launch_check("rel_l2_kernel"));
+  double h[2];
+  MX_CUDA_TRY(cudaMemcpyAsync(h, ctx->red2, sizeof(h), cudaMemcpyDeviceToHost, st));
+  MX_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = h[1] > 0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
+  return MX_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,737 @@
+// Learned demag surrogate: a 3D conv net 3 -> 32 -> 64 -> 32 -> 3 (3x3x3
+// kernels, zero padding 1, exact-erf GELU after the first three layers) that
+// maps the normalised magnetisation to the normalised demag field, trained
+// with SmoothL1 loss and Adam with L2 weight decay (the paper's ML module,
+// Sec. II-D: a network trained offline on (M, H_demag) pairs from the FFT
+// solver, per-channel Gaussian normaliser, Adam lr 1e-3, weight decay 1e-4).
+//
+// Activations are BF16, channels-last [b][z][y][x][C] with C padded to a
+// multiple of 16 (first input: 3 -> 16); weights are FP32 masters with BF16
+// copies for the tensor cores.  Every convolution is an implicit GEMM on
+// mma.sync m16n8k16 (BF16 in, FP32 accumulate): a block takes a 16 x 8 x 1
+// tile of output cells (one warp per row of 16 cells) and a (18 x 10 x 3)
+// halo of input cells staged with cp.async; all 27 taps of the layer's
+// weights stay in shared memory.
+//   forward     out = conv(a, W) + b, stored pre-activation y and a = gelu(y)
+//   backward-x  dA_{l-1} = conv(dY_l, W'), W'[tap][ci][co] = W[26 - tap][co][ci],
+//               times gelu'(y_{l-1}) in the epilogue -> dY_{l-1}
+//   backward-W  dW[tap] = sum over cells of dY (x) x_shifted(tap), one block per
+//               (tap, chunk of tiles), FP32 atomics into the gradient
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mx {
+
+constexpr int kTX = 16, kTY = 8;             // output tile (cells)
+constexpr int kHX = kTX + 2, kHY = kTY + 2;  // halo
+constexpr int kHalo = kHX * kHY * 3;
+constexpr int kCnnThreads = 256;
+static const int kCh[5] = {3, 32, 64, 32, 3};
+static const int kCinPad[4] = {16, 32, 64, 32};
+static const int kCoutPad[4] = {32, 64, 32, 8};
+
+typedef unsigned short bf16_t;
+
+__device__ __forceinline__ bf16_t f2bf(float f) {
+  const __nv_bfloat16_raw r = __float2bfloat16_rn(f);
+  return r.x;
+}
+__device__ __forceinline__ float bf2f(bf16_t h) {
+  __nv_bfloat16_raw r;
+  r.x = h;
+  return __bfloat162float(r);
+}
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  return (uint32_t)f2bf(a) | ((uint32_t)f2bf(b) << 16);
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, bool valid) {
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(g), "r"(n));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+__device__ __forceinline__ float gelu_f(float y) { return 0.5f * y * (1.f + erff(y * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float y) {
+  return 0.5f * (1.f + erff(y * 0.70710678118654752f)) + y * 0.39894228040143268f * expf(-0.5f * y * y);
+}
+
+struct ConvDims {
+  int nx, ny, nz, batch;
+  int tiles_x, tiles_y, ntiles;  // tiles per (b, z) plane and total
+};
+
+__host__ __device__ inline void tile_coords(const ConvDims& d, int t, int& b, int& z, int& y0, int& x0) {
+  const int tx = t % d.tiles_x;
+  int r = t / d.tiles_x;
+  const int ty = r % d.tiles_y;
+  r /= d.tiles_y;
+  z = r % d.nz;
+  b = r / d.nz;
+  y0 = ty * kTY;
+  x0 = tx * kTX;
+}
+
+enum ConvMode { CM_HIDDEN = 0, CM_LAST = 1, CM_BWD = 2 };
+
+// ---------------------------------------------------------------------------
+// Convolution: in [cells][CIN] (bf16), weights wk [27][COUT][CIN] (bf16),
+// one persistent block per SM looping over tiles.
+//   CM_HIDDEN: ypre = acc + b (bf16), out = gelu(acc + b) (bf16), [cells][COUT]
+//   CM_LAST:   outf = acc + b (fp32) channels 0..2 of a float4 record per cell
+//   CM_BWD:    out = acc * gelu'(ypre) (bf16), [cells][COUT]  (ypre read)
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(kCnnThreads, 1) conv_kernel(const bf16_t* __restrict__ in,
+                                                               const bf16_t* __restrict__ wk,
+                                                               const float* __restrict__ bias, bf16_t* __restrict__ out,
+                                                               bf16_t* __restrict__ ypre, float4* __restrict__ outf,
+                                                               ConvDims d) {
+  constexpr int CP = CIN + 8;   // smem pitch (elements) of a halo cell / weight row
+  constexpr int NT = COUT / 8;  // n tiles of 8
+  extern __shared__ __align__(16) unsigned char smraw[];
+  bf16_t* sw = (bf16_t*)smraw;                 // [27][COUT][CP]
+  bf16_t* sh = sw + 27 * COUT * CP;            // [kHalo][CP]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // weights: 27*COUT rows of CIN, 16-byte chunks
+  for (int e = tid; e < 27 * COUT * (CIN / 8); e += kCnnThreads) {
+    const int row = e / (CIN / 8), ch = e % (CIN / 8);
+    cp_async16(smem_u32(sw + row * CP + ch * 8), wk + (long)row * CIN + ch * 8, true);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const long plane = (long)d.nx * d.ny;
+  for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+    int b, z, y0, x0;
+    tile_coords(d, t, b, z, y0, x0);
+    // halo cells (hz, hy, hx) -> input cell (z + hz - 1, y0 + hy - 1, x0 + hx - 1)
+    for (int e = tid; e < kHalo * (CIN / 8); e += kCnnThreads) {
+      const int hc = e / (CIN / 8), ch = e % (CIN / 8);
+      const int hx = hc % kHX, hy = (hc / kHX) % kHY, hz = hc / (kHX * kHY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
+      const bool ok = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 && gz < d.nz;
+      const long cell = ok ? ((long)b * d.nz + gz) * plane + (long)gy * d.nx + gx : 0;
+      cp_async16(smem_u32(sh + hc * CP + ch * 8), in + cell * CIN + ch * 8, ok);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    // A rows: cell (x = row, y = warp); ldmatrix lane -> (row, k half)
+    const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
+    const int akof = (lane >> 4) * 8;
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+      const int hc = (dz * kHY + warp + dy) * kHX + arow + dx;
+      const bf16_t* arowp = sh + hc * CP + akof;
+      const bf16_t* wt = sw + tap * COUT * CP;
+#pragma unroll
+      for (int kc = 0; kc < CIN / 16; ++kc) {
+        uint32_t a0, a1, a2, a3;
+        ldsm_x4(smem_u32(arowp + kc * 16), a0, a1, a2, a3);
+#pragma unroll
+        for (int n = 0; n < NT; n += 2) {
+          if (n + 1 < NT) {
+            // two n tiles: lanes 0-7 (n, k0), 8-15 (n, k8), 16-23 (n+8, k0), 24-31 (n+8, k8)
+            const int wrow = n * 8 + (lane & 7) + ((lane >> 4) << 3);
+            const int wk8 = ((lane >> 3) & 1) * 8;
+            uint32_t b0, b1, b2, b3;
+            ldsm_x4(smem_u32(wt + wrow * CP + kc * 16 + wk8), b0, b1, b2, b3);
+            mma16816(acc[n], a0, a1, a2, a3, b0, b1);
+            mma16816(acc[n + 1], a0, a1, a2, a3, b2, b3);
+          } else {
+            const int wrow = n * 8 + (lane & 7);
+            const int wk8 = ((lane >> 3) & 1) * 8;
+            uint32_t b0, b1;
+            ldsm_x2(smem_u32(wt + wrow * CP + kc * 16 + wk8), b0, b1);
+            mma16816(acc[n], a0, a1, a2, a3, b0, b1);
+          }
+        }
+      }
+    }
+    // epilogue: thread holds rows g, g+8 (cells x0+g, x0+g+8 of row y0+warp), cols 8n + 2q, +1
+    const int g = lane >> 2, q = lane & 3;
+    const int gy = y0 + warp;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int gx = x0 + g + half * 8;
+      if (gx >= d.nx || gy >= d.ny) continue;
+      const long cell = ((long)b * d.nz + z) * plane + (long)gy * d.nx + gx;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const int c0 = n * 8 + 2 * q;
+        float v0 = acc[n][2 * half], v1 = acc[n][2 * half + 1];
+        if (MODE == CM_HIDDEN) {
+          v0 += bias[c0];
+          v1 += bias[c0 + 1];
+          *(uint32_t*)(ypre + cell * COUT + c0) = pack2(v0, v1);
+          *(uint32_t*)(out + cell * COUT + c0) = pack2(gelu_f(v0), gelu_f(v1));
+        } else if (MODE == CM_BWD) {
+          const uint32_t yp = *(const uint32_t*)(ypre + cell * COUT + c0);
+          const float y0f = bf2f((bf16_t)(yp & 0xffff)), y1f = bf2f((bf16_t)(yp >> 16));
+          *(uint32_t*)(out + cell * COUT + c0) = pack2(v0 * gelu_grad(y0f), v1 * gelu_grad(y1f));
+        } else {
+          float* o = (float*)(outf + cell);
+          if (c0 < 3) o[c0] = v0 + bias[c0];
+          if (c0 + 1 < 3) o[c0 + 1] = v1 + bias[c0 + 1];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient of one layer: dW[tap][co][ci] += sum_cells dY[cell][co] *
+// x[cell + off(tap)][ci].  Block (tap, chunk): M = COUT rows (16 per m tile),
+// N = CIN, K = cells.  dY is [cells][COUT] (COUT padded to 16), x [cells][CIN].
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __restrict__ x, const bf16_t* __restrict__ dy,
+                                                            float* __restrict__ dw, ConvDims d, int cin_real,
+                                                            int cout_real, int tiles_per_block) {
+  constexpr int XP = CIN + 8, YP = COUT + 8;
+  constexpr int MT = COUT / 16, NTL = CIN / 8;  // m tiles of 16, n tiles of 8
+  constexpr int TILES = MT * NTL;
+  constexpr int PER_WARP = (TILES + 7) / 8;
+  __shared__ __align__(16) bf16_t sx[kTX * kTY * XP];
+  __shared__ __align__(16) bf16_t sy[kTX * kTY * YP];
+  const int tap = blockIdx.y;
+  const int dz = tap / 9, ddy = (tap / 3) % 3, ddx = tap % 3;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float acc[PER_WARP][4];
+#pragma unroll
+  for (int i = 0; i < PER_WARP; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  const long plane = (long)d.nx * d.ny;
+  const int t0 = blockIdx.x * tiles_per_block;
+  const int t1 = min(d.ntiles, t0 + tiles_per_block);
+  for (int t = t0; t < t1; ++t) {
+    int b, z, y0, x0;
+    tile_coords(d, t, b, z, y0, x0);
+    for (int e = tid; e < kTX * kTY * (CIN / 8); e += kCnnThreads) {
+      const int c = e / (CIN / 8), ch = e % (CIN / 8);
+      const int cx = c % kTX, cy = c / kTX;
+      const int ox = x0 + cx, oy = y0 + cy;
+      const int gx = ox + ddx - 1, gy = oy + ddy - 1, gz = z + dz - 1;
+      const bool ok = ox < d.nx && oy < d.ny && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 &&
+                      gz < d.nz;
+      const long cell = ok ? ((long)b * d.nz + gz) * plane + (long)gy * d.nx + gx : 0;
+      cp_async16(smem_u32(sx + c * XP + ch * 8), x + cell * CIN + ch * 8, ok);
+    }
+    for (int e = tid; e < kTX * kTY * (COUT / 8); e += kCnnThreads) {
+      const int c = e / (COUT / 8), ch = e % (COUT / 8);
+      const int ox = x0 + c % kTX, oy = y0 + c / kTX;
+      const bool ok = ox < d.nx && oy < d.ny;
+      const long cell = ok ? ((long)b * d.nz + z) * plane + (long)oy * d.nx + ox : 0;
+      cp_async16(smem_u32(sy + c * YP + ch * 8), dy + cell * COUT + ch * 8, ok);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER_WARP; ++i) {
+      const int tile = warp * PER_WARP + i;
+      if (tile >= TILES) break;
+      const int mt = tile / NTL, nt = tile % NTL;
+      for (int kc = 0; kc < kTX * kTY / 16; ++kc) {
+        // A = dY^T (co x cells): stored [cell][co] -> transposed loads
+        uint32_t a0, a1, a2, a3;
+        {
+          const int krow = kc * 16 + (lane & 7) + ((lane >> 4) << 3);
+          const int mcol = mt * 16 + ((lane >> 3) & 1) * 8;
+          ldsm_x4_t(smem_u32(sy + krow * YP + mcol), a0, a1, a2, a3);
+        }
+        // B = x (cells x ci), col layout from row-major [cell][ci] by transposed loads
+        uint32_t b0, b1;
+        {
+          const int krow = kc * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+          uint32_t r0, r1, r2, r3;
+          ldsm_x4_t(smem_u32(sx + krow * XP + nt * 8), r0, r1, r2, r3);
+          b0 = r0;
+          b1 = r1;
+          (void)r2;
+          (void)r3;
+        }
+        mma16816(acc[i], a0, a1, a2, a3, b0, b1);
+      }
+    }
+    __syncthreads();
+  }
+  // accumulate: rows co = mt*16 + g (+8), cols ci = nt*8 + 2q (+1)
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int i = 0; i < PER_WARP; ++i) {
+    const int tile = warp * PER_WARP + i;
+    if (tile >= TILES) break;
+    const int mt = tile / NTL, nt = tile % NTL;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int co = mt * 16 + g + (r >= 2 ? 8 : 0);
+      const int ci = nt * 8 + 2 * q + (r & 1);
+      if (co < cout_real && ci < cin_real) atomicAdd(&dw[((long)co * cin_real + ci) * 27 + tap], acc[i][r]);
+    }
+  }
+}
+
+// bias gradient: db[co] += sum over cells of dY[cell][co]
+__global__ void bgrad_kernel(const bf16_t* __restrict__ dy, int cpad, int creal, long ncells, float* __restrict__ db) {
+  const int co = threadIdx.x % 64;
+  const int lane_grp = threadIdx.x / 64;  // 4 groups
+  if (co >= creal) return;
+  float s = 0.f;
+  for (long c = (long)blockIdx.x * 4 + lane_grp; c < ncells; c += (long)gridDim.x * 4) s += bf2f(dy[c * cpad + co]);
+  atomicAdd(&db[co], s);
+}
+
+// input normalisation: m float4 -> x0 bf16 [cells][16]
+__global__ void normalize_in_kernel(const float4* __restrict__ m, bf16_t* __restrict__ x0, long ncells, float3 mean,
+                                    float3 inv_std) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const float4 v = m[c];
+  uint4 lo, hi;
+  lo.x = pack2((v.x - mean.x) * inv_std.x, (v.y - mean.y) * inv_std.y);
+  lo.y = pack2((v.z - mean.z) * inv_std.z, 0.f);
+  lo.z = lo.w = 0u;
+  hi.x = hi.y = hi.z = hi.w = 0u;
+  uint4* o = (uint4*)(x0 + c * 16);
+  o[0] = lo;
+  o[1] = hi;
+}
+
+// output: normalised prediction (float4) -> H = pred * std + mean
+__global__ void denormalize_out_kernel(const float4* __restrict__ pred, float4* __restrict__ h, long ncells,
+                                       float3 mean, float3 std) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const float4 p = pred[c];
+  h[c] = make_float4(p.x * std.x + mean.x, p.y * std.y + mean.y, p.z * std.z + mean.z, 0.f);
+}
+
+// SmoothL1 (beta 1) of pred against the normalised target; dY4 [cells][16] bf16
+__global__ void loss_kernel(const float4* __restrict__ pred, const float4* __restrict__ h_target, long ncells,
+                            float3 mean, float3 inv_std, float inv_count, bf16_t* __restrict__ dy4,
+                            float* __restrict__ loss) {
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (c < ncells) {
+    const float4 p = pred[c];
+    const float4 t = h_target[c];
+    const float d0 = p.x - (t.x - mean.x) * inv_std.x;
+    const float d1 = p.y - (t.y - mean.y) * inv_std.y;
+    const float d2 = p.z - (t.z - mean.z) * inv_std.z;
+    const float ds[3] = {d0, d1, d2};
+    float g[3];
+    for (int k = 0; k < 3; ++k) {
+      const float a = fabsf(ds[k]);
+      l += a < 1.f ? 0.5f * ds[k] * ds[k] : a - 0.5f;
+      g[k] = fminf(fmaxf(ds[k], -1.f), 1.f) * inv_count;
+    }
+    uint4 lo, hi;
+    lo.x = pack2(g[0], g[1]);
+    lo.y = pack2(g[2], 0.f);
+    lo.z = lo.w = 0u;
+    hi.x = hi.y = hi.z = hi.w = 0u;
+    uint4* o = (uint4*)(dy4 + c * 16);
+    o[0] = lo;
+    o[1] = hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, l * inv_count);
+}
+
+// FP32 master weights -> bf16 [27][COUT_PAD][CIN_PAD] (forward) and the
+// flipped, transposed copy [27][CIN_PAD'][COUT_PAD'] for the backward pass.
+__global__ void pack_weights_kernel(const float* __restrict__ W, int cin, int cout, bf16_t* __restrict__ fwd,
+                                    int cin_pad, int cout_pad, bf16_t* __restrict__ bwd, int bwd_in_pad,
+                                    int bwd_out_pad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = 27 * cout_pad * cin_pad;
+  if (e < nf) {
+    const int ci = e % cin_pad, co = (e / cin_pad) % cout_pad, tap = e / (cin_pad * cout_pad);
+    const float v = (ci < cin && co < cout) ? W[((long)co * cin + ci) * 27 + tap] : 0.f;
+    fwd[e] = f2bf(v);
+  }
+  if (bwd) {
+    const int nb = 27 * bwd_out_pad * bwd_in_pad;
+    if (e < nb) {
+      // backward conv: input channels = this layer's cout, output channels = cin
+      const int co = e % bwd_in_pad, ci = (e / bwd_in_pad) % bwd_out_pad, tapb = e / (bwd_in_pad * bwd_out_pad);
+      const int tap = 26 - tapb;
+      const float v = (ci < cin && co < cout) ? W[((long)co * cin + ci) * 27 + tap] : 0.f;
+      bwd[e] = f2bf(v);
+    }
+  }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long n, float lr, float wd, float b1, float b2, float c1, float c2,
+                            float eps) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i] + wd * p[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace mx
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using mx::bf16_t;
+
+struct mx_cnn {
+  int nx, ny, nz, max_batch;
+  long cells;
+  float* params = nullptr;  // FP32 masters, oracle order (W1, b1, ..., W4, b4)
+  float* grad = nullptr;
+  float* am = nullptr;
+  float* av = nullptr;
+  int adam_t = 0;
+  bf16_t* wf[4] = {nullptr, nullptr, nullptr, nullptr};
+  bf16_t* wb[4] = {nullptr, nullptr, nullptr, nullptr};
+  bf16_t *x0 = nullptr, *a1 = nullptr, *y1 = nullptr, *a2 = nullptr, *y2 = nullptr, *a3 = nullptr, *y3 = nullptr;
+  bf16_t *dy4 = nullptr, *dy3 = nullptr, *dy2 = nullptr, *dy1 = nullptr;
+  float4* pred = nullptr;
+  float* loss = nullptr;
+  float stats[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 1, 1, 1};
+};
+
+namespace mx {
+
+static long layer_w_off(int l) {
+  long o = 0;
+  for (int q = 0; q < l; ++q) o += (long)kCh[q] * kCh[q + 1] * 27 + kCh[q + 1];
+  return o;
+}
+static long num_params_total() { return layer_w_off(4); }
+
+static ConvDims conv_dims(const mx_cnn* n, int batch) {
+  ConvDims d;
+  d.nx = n->nx;
+  d.ny = n->ny;
+  d.nz = n->nz;
+  d.batch = batch;
+  d.tiles_x = (n->nx + kTX - 1) / kTX;
+  d.tiles_y = (n->ny + kTY - 1) / kTY;
+  d.ntiles = d.tiles_x * d.tiles_y * n->nz * batch;
+  return d;
+}
+
+template <int CIN, int COUT, int MODE> static size_t conv_smem() {
+  return sizeof(bf16_t) * (27 * COUT + kHalo) * (CIN + 8);
+}
+
+static int g_num_sms = 0;
+
+template <int CIN, int COUT, int MODE>
+static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf16_t* out, bf16_t* ypre, float4* outf,
+                          const ConvDims& d, cudaStream_t st) {
+  const size_t sm = conv_smem<CIN, COUT, MODE>();
+  static bool attr = false;
+  if (!attr) {
+    MX_CUDA_TRY(cudaFuncSetAttribute(conv_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+    attr = true;
+  }
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  const int grid = d.ntiles < g_num_sms ? d.ntiles : g_num_sms;
+  conv_kernel<CIN, COUT, MODE><<<grid, kCnnThreads, sm, st>>>(in, w, b, out, ypre, outf, d);
+  return launch_check("conv_kernel");
+}
+
+template <int CIN, int COUT>
+static mx_status wgrad_run(const bf16_t* x, const bf16_t* dy, float* dw, const ConvDims& d, int cin_real,
+                           int cout_real, cudaStream_t st) {
+  int tpb = d.ntiles / 32;
+  if (tpb < 1) tpb = 1;
+  dim3 grid((d.ntiles + tpb - 1) / tpb, 27);
+  wgrad_kernel<CIN, COUT><<<grid, kCnnThreads, 0, st>>>(x, dy, dw, d, cin_real, cout_real, tpb);
+  return launch_check("wgrad_kernel");
+}
+
+static mx_status pack_all(mx_cnn* n, cudaStream_t st) {
+  // forward packs [27][coutpad][cinpad]; backward packs for layers 2..4
+  const int bw_in[4] = {0, 64, 32, 16};   // backward conv input channels (this layer's cout, padded)
+  const int bw_out[4] = {0, 32, 64, 32};  // backward conv output channels (this layer's cin)
+  for (int l = 0; l < 4; ++l) {
+    const int cin = kCh[l], cout = kCh[l + 1];
+    const int nf = 27 * kCoutPad[l] * kCinPad[l];
+    const int nb = l > 0 ? 27 * bw_in[l] * bw_out[l] : 0;
+    const int ne = nf > nb ? nf : nb;
+    pack_weights_kernel<<<(ne + 255) / 256, 256, 0, st>>>(n->params + layer_w_off(l), cin, cout, n->wf[l], kCinPad[l],
+                                                          kCoutPad[l], l > 0 ? n->wb[l] : nullptr, bw_in[l], bw_out[l]);
+    MX_TRY(launch_check("pack_weights_kernel"));
+  }
+  return MX_OK;
+}
+
+static mx_status cnn_forward_to_pred(mx_cnn* n, const float4* m, int batch, cudaStream_t st) {
+  const long nc = n->cells * batch;
+  const float* s = n->stats;
+  normalize_in_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+      m, n->x0, nc, make_float3(s[0], s[1], s[2]), make_float3(1.f / s[3], 1.f / s[4], 1.f / s[5]));
+  MX_TRY(launch_check("normalize_in_kernel"));
+  const ConvDims d = conv_dims(n, batch);
+  const float* P = n->params;
+  MX_TRY((conv_run<16, 32, CM_HIDDEN>(n->x0, n->wf[0], P + layer_w_off(0) + 32 * 3 * 27, n->a1, n->y1, nullptr, d, st)));
+  MX_TRY((conv_run<32, 64, CM_HIDDEN>(n->a1, n->wf[1], P + layer_w_off(1) + 64 * 32 * 27, n->a2, n->y2, nullptr, d, st)));
+  MX_TRY((conv_run<64, 32, CM_HIDDEN>(n->a2, n->wf[2], P + layer_w_off(2) + 32 * 64 * 27, n->a3, n->y3, nullptr, d, st)));
+  MX_TRY((conv_run<32, 8, CM_LAST>(n->a3, n->wf[3], P + layer_w_off(3) + 3 * 32 * 27, nullptr, nullptr, n->pred, d, st)));
+  return MX_OK;
+}
+
+bool cnn_matches(const mx_cnn* n, const Grid& g) { return n->nx == g.nx && n->ny == g.ny && n->nz == g.nz; }
+
+mx_status cnn_demag(mx_cnn* n, const float4* m, float4* h, cudaStream_t st) {
+  MX_TRY(cnn_forward_to_pred(n, m, 1, st));
+  const float* s = n->stats;
+  denormalize_out_kernel<<<(unsigned)((n->cells + 255) / 256), 256, 0, st>>>(
+      n->pred, h, n->cells, make_float3(s[6], s[7], s[8]), make_float3(s[9], s[10], s[11]));
+  return launch_check("denormalize_out_kernel");
+}
+
+}  // namespace mx
+
+using namespace mx;
+
+extern "C" {
+
+int mx_cnn_num_params(void) { return (int)num_params_total(); }
+
+mx_status mx_cnn_destroy(mx_cnn* n) {
+  if (!n) return MX_OK;
+  void* ptrs[] = {n->params, n->grad, n->am, n->av, n->wf[0], n->wf[1], n->wf[2], n->wf[3], n->wb[1], n->wb[2],
+                  n->wb[3], n->x0, n->a1, n->y1, n->a2, n->y2, n->a3, n->y3, n->dy4, n->dy3, n->dy2, n->dy1,
+                  n->pred, n->loss};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete n;
+  return MX_OK;
+}
+
+mx_status mx_cnn_create(mx_cnn** out, int nx, int ny, int nz, int max_batch) {
+  clear_error();
+  if (!out || nx < 1 || ny < 1 || nz < 1 || max_batch < 1) {
+    set_error("mx_cnn_create: need out != NULL and nx, ny, nz, max_batch >= 1");
+    return MX_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  mx_cnn* n = new mx_cnn();
+  n->nx = nx;
+  n->ny = ny;
+  n->nz = nz;
+  n->max_batch = max_batch;
+  n->cells = (long)nx * ny * nz;
+  const long nc = n->cells * max_batch;
+  const long np = num_params_total();
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
+  };
+  alloc((void**)&n->params, sizeof(float) * np);
+  alloc((void**)&n->grad, sizeof(float) * np);
+  alloc((void**)&n->am, sizeof(float) * np);
+  alloc((void**)&n->av, sizeof(float) * np);
+  const int bw_in[4] = {0, 64, 32, 16}, bw_out[4] = {0, 32, 64, 32};
+  for (int l = 0; l < 4; ++l) {
+    alloc((void**)&n->wf[l], sizeof(bf16_t) * 27 * kCoutPad[l] * kCinPad[l]);
+    if (l > 0) alloc((void**)&n->wb[l], sizeof(bf16_t) * 27 * bw_in[l] * bw_out[l]);
+  }
+  alloc((void**)&n->x0, sizeof(bf16_t) * nc * 16);
+  alloc((void**)&n->a1, sizeof(bf16_t) * nc * 32);
+  alloc((void**)&n->y1, sizeof(bf16_t) * nc * 32);
+  alloc((void**)&n->a2, sizeof(bf16_t) * nc * 64);
+  alloc((void**)&n->y2, sizeof(bf16_t) * nc * 64);
+  alloc((void**)&n->a3, sizeof(bf16_t) * nc * 32);
+  alloc((void**)&n->y3, sizeof(bf16_t) * nc * 32);
+  alloc((void**)&n->dy4, sizeof(bf16_t) * nc * 16);
+  alloc((void**)&n->dy3, sizeof(bf16_t) * nc * 32);
+  alloc((void**)&n->dy2, sizeof(bf16_t) * nc * 64);
+  alloc((void**)&n->dy1, sizeof(bf16_t) * nc * 32);
+  alloc((void**)&n->pred, sizeof(float4) * nc);
+  alloc((void**)&n->loss, sizeof(float));
+  if (!ok) {
+    mx_cnn_destroy(n);
+    set_error("mx_cnn_create: device allocation failed");
+    return MX_ERR_OOM;
+  }
+  if (cudaMemset(n->params, 0, sizeof(float) * np) != cudaSuccess ||
+      cudaMemset(n->am, 0, sizeof(float) * np) != cudaSuccess ||
+      cudaMemset(n->av, 0, sizeof(float) * np) != cudaSuccess) {
+    mx_cnn_destroy(n);
+    set_error("mx_cnn_create: memset failed");
+    return MX_ERR_CUDA;
+  }
+  *out = n;
+  return MX_OK;
+}
+
+mx_status mx_cnn_set_params(mx_cnn* n, const float* params, mx_stream_t stream) {
+  if (!n || !params) {
+    set_error("mx_cnn_set_params: NULL argument");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  MX_CUDA_TRY(cudaMemcpyAsync(n->params, params, sizeof(float) * num_params_total(), cudaMemcpyDeviceToDevice, st));
+  MX_CUDA_TRY(cudaMemsetAsync(n->am, 0, sizeof(float) * num_params_total(), st));
+  MX_CUDA_TRY(cudaMemsetAsync(n->av, 0, sizeof(float) * num_params_total(), st));
+  n->adam_t = 0;
+  return pack_all(n, st);
+}
+
+mx_status mx_cnn_get_params(const mx_cnn* n, float* params, mx_stream_t stream) {
+  if (!n || !params) {
+    set_error("mx_cnn_get_params: NULL argument");
+    return MX_ERR_INVALID_ARG;
+  }
+  MX_CUDA_TRY(cudaMemcpyAsync(params, n->params, sizeof(float) * num_params_total(), cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+  return MX_OK;
+}
+
+mx_status mx_cnn_set_normalizer(mx_cnn* n, const double stats[12]) {
+  if (!n || !stats) {
+    set_error("mx_cnn_set_normalizer: NULL argument");
+    return MX_ERR_INVALID_ARG;
+  }
+  for (int q = 0; q < 12; ++q) {
+    if (!isfinite(stats[q]) || ((q % 6) >= 3 && !(stats[q] > 0))) {
+      set_error("mx_cnn_set_normalizer: standard deviations must be > 0 and every entry finite");
+      return MX_ERR_INVALID_ARG;
+    }
+    n->stats[q] = (float)stats[q];
+  }
+  return MX_OK;
+}
+
+static mx_status check_batch(const mx_cnn* n, const float* m, int batch, const char* what) {
+  if (!n || !m || batch < 1 || batch > n->max_batch || (((uintptr_t)m) & 15)) {
+    set_error(std::string(what) + ": bad network, pointer or batch (1..max_batch)");
+    return MX_ERR_INVALID_ARG;
+  }
+  return MX_OK;
+}
+
+mx_status mx_cnn_forward(mx_cnn* n, const float* m, float* h, int batch, mx_stream_t stream) {
+  MX_TRY(check_batch(n, m, batch, "mx_cnn_forward"));
+  if (!h || (((uintptr_t)h) & 15)) {
+    set_error("mx_cnn_forward: h must be a 16-byte aligned device pointer");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  MX_TRY(cnn_forward_to_pred(n, (const float4*)m, batch, st));
+  const float* s = n->stats;
+  const long nc = n->cells * batch;
+  denormalize_out_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+      n->pred, (float4*)h, nc, make_float3(s[6], s[7], s[8]), make_float3(s[9], s[10], s[11]));
+  return launch_check("denormalize_out_kernel");
+}
+
+mx_status mx_cnn_loss_grad(mx_cnn* n, const float* m, const float* h_target, int batch, float* loss_out,
+                           float* grad_out, mx_stream_t stream) {
+  MX_TRY(check_batch(n, m, batch, "mx_cnn_loss_grad"));
+  if (!h_target || (((uintptr_t)h_target) & 15)) {
+    set_error("mx_cnn_loss_grad: h_target must be a 16-byte aligned device pointer");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  MX_TRY(cnn_forward_to_pred(n, (const float4*)m, batch, st));
+  const long nc = n->cells * batch;
+  const long np = num_params_total();
+  MX_CUDA_TRY(cudaMemsetAsync(n->loss, 0, sizeof(float), st));
+  MX_CUDA_TRY(cudaMemsetAsync(n->grad, 0, sizeof(float) * np, st));
+  const float* s = n->stats;
+  loss_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(
+      n->pred, (const float4*)h_target, nc, make_float3(s[6], s[7], s[8]),
+      make_float3(1.f / s[9], 1.f / s[10], 1.f / s[11]), 1.f / (3.f * (float)nc), n->dy4, n->loss);
+  MX_TRY(launch_check("loss_kernel"));
+  const ConvDims d = conv_dims(n, batch);
+  float* G = n->grad;
+  const unsigned bgrid = (unsigned)((nc + 1023) / 1024 < 1024 ? (nc + 1023) / 1024 : 1024);
+  // layer 4: weights, bias, then dY3 = conv(dY4, W4') * gelu'(y3)
+  MX_TRY((wgrad_run<32, 16>(n->a3, n->dy4, G + layer_w_off(3), d, 32, 3, st)));
+  bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy4, 16, 3, nc, G + layer_w_off(3) + 3 * 32 * 27);
+  MX_TRY(launch_check("bgrad_kernel"));
+  MX_TRY((conv_run<16, 32, CM_BWD>(n->dy4, n->wb[3], nullptr, n->dy3, n->y3, nullptr, d, st)));
+  // layer 3
+  MX_TRY((wgrad_run<64, 32>(n->a2, n->dy3, G + layer_w_off(2), d, 64, 32, st)));
+  bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy3, 32, 32, nc, G + layer_w_off(2) + 32 * 64 * 27);
+  MX_TRY(launch_check("bgrad_kernel"));
+  MX_TRY((conv_run<32, 64, CM_BWD>(n->dy3, n->wb[2], nullptr, n->dy2, n->y2, nullptr, d, st)));
+  // layer 2
+  MX_TRY((wgrad_run<32, 64>(n->a1, n->dy2, G + layer_w_off(1), d, 32, 64, st)));
+  bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy2, 64, 64, nc, G + layer_w_off(1) + 64 * 32 * 27);
+  MX_TRY(launch_check("bgrad_kernel"));
+  MX_TRY((conv_run<64, 32, CM_BWD>(n->dy2, n->wb[1], nullptr, n->dy1, n->y1, nullptr, d, st)));
+  // layer 1
+  MX_TRY((wgrad_run<16, 32>(n->x0, n->dy1, G + layer_w_off(0), d, 3, 32, st)));
+  bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy1, 32, 32, nc, G + layer_w_off(0) + 32 * 3 * 27);
+  MX_TRY(launch_check("bgrad_kernel"));
+  if (loss_out) MX_CUDA_TRY(cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (grad_out) MX_CUDA_TRY(cudaMemcpyAsync(grad_out, n->grad, sizeof(float) * np, cudaMemcpyDeviceToDevice, st));
+  return MX_OK;
+}
+
+mx_status mx_cnn_adam_step(mx_cnn* n, double lr, double weight_decay, mx_stream_t stream) {
+  if (!n || !(lr > 0) || !(weight_decay >= 0)) {
+    set_error("mx_cnn_adam_step: need a network, lr > 0 and weight_decay >= 0");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  n->adam_t += 1;
+  const double b1 = 0.9, b2 = 0.999;
+  const double c1 = 1.0 - pow(b1, n->adam_t), c2 = 1.0 - pow(b2, n->adam_t);
+  const long np = num_params_total();
+  adam_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(n->params, n->grad, n->am, n->av, np, (float)lr,
+                                                            (float)weight_decay, (float)b1, (float)b2, (float)c1,
+                                                            (float)c2, 1e-8f);
+  MX_TRY(launch_check("adam_kernel"));
+  return pack_all(n, st);
+}
+
+}  // extern "C"

@@ -148,4 +148,8 @@ struct mx_ctx {
 
   // adjoint workspaces (mx_adjoint_reserve)
   mx::AdjWork* adj = nullptr;
+
+  // learned demag backend (mx_set_demag_surrogate); NULL: FFT convolution
+  struct mx_cnn* surrogate = nullptr;
+  double* red2 = nullptr;         // 2 FP64 accumulators for mx_rel_l2
 };

@@ -1,0 +1,126 @@
+"""Learned demag surrogate on the GPU vs the FP64 oracle network.
+
+Tolerances (BF16 activations and weights, FP32 accumulation): the forward pass
+is compared with an oracle that rounds inputs, weights and hidden activations
+to BF16 at the same places, so only FP32-vs-FP64 accumulation and rare
+rounding-boundary flips differ: relative L2 <= 1e-3.  The gradient also passes
+through BF16-stored backward activations (relative error 2^-9 each):
+relative L2 <= 1e-2.  Adam is elementwise FP32: 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from helpers import cfg_of, context, rel_l2
+from oracle import cnn as ocnn
+
+pytestmark = pytest.mark.gpu
+
+
+def _net(shape, batch, seed=7):
+    from paper_2602_12242_gb300.surrogate import Surrogate
+    nz, ny, nx = shape
+    net = Surrogate(nx, ny, nz, max_batch=batch)
+    flat = ocnn.init_params(seed)
+    net.set_params(torch.as_tensor(flat, dtype=torch.float32))
+    return net, flat.astype(np.float32).astype(np.float64)
+
+
+def _fields(shape, batch, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.normal(size=(batch,) + shape + (3,))
+    m /= np.linalg.norm(m, axis=-1, keepdims=True)
+    return m
+
+
+def _dev(a):
+    from paper_2602_12242_gb300.solver import to_dev4
+    return torch.stack([to_dev4(x) for x in a])
+
+
+STATS = [0.05, -0.02, 0.1, 0.55, 0.6, 0.5, 1e3, -2e3, 5e3, 1.5e5, 1.4e5, 2.2e5]
+
+
+def _oracle_forward(flat, m, stats):
+    mean_in, std_in = np.array(stats[0:3]), np.array(stats[3:6])
+    mean_out, std_out = np.array(stats[6:9]), np.array(stats[9:12])
+    x = ocnn.to_ncdhw((m - mean_in) / std_in)
+    # the GPU normalises in FP32 before rounding
+    x = torch.as_tensor(np.asarray(((m - mean_in.astype(np.float32)) / std_in.astype(np.float32)),
+                                   dtype=np.float32), dtype=torch.float64)
+    x = ocnn.to_ncdhw(x)
+    y = ocnn.forward(ocnn.unflatten(flat), x, rnd=ocnn.bf16_round)
+    return ocnn.from_ncdhw(y).numpy() * std_out + mean_out
+
+
+@pytest.mark.parametrize("shape,batch", [((3, 20, 24), 2), ((4, 64, 64), 1), ((1, 9, 5), 1)])
+def test_forward_matches_oracle(shape, batch):
+    net, flat = _net(shape, batch)
+    net.set_normalizer(STATS)
+    m = _fields(shape, batch, 51).astype(np.float32).astype(np.float64)
+    h = net.forward(_dev(m) if batch > 1 else _dev(m)[0])
+    got = h[..., :3].double().cpu().numpy().reshape((batch,) + shape + (3,))
+    ref = _oracle_forward(flat, m, STATS)
+    assert rel_l2(got, ref) <= 1e-3, rel_l2(got, ref)
+
+
+def test_loss_and_gradient_match_oracle():
+    shape, batch = (3, 20, 24), 2
+    net, flat = _net(shape, batch)
+    net.set_normalizer(STATS)
+    m = _fields(shape, batch, 52).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(53)
+    tgt = (np.array(STATS[6:9]) + np.array(STATS[9:12]) * rng.normal(size=(batch,) + shape + (3,)))
+    tgt = tgt.astype(np.float32).astype(np.float64)
+    loss, grad = net.loss_grad(_dev(m), _dev(tgt))
+    # oracle: same rounded forward, loss on the normalised target, FP64 autograd
+    mean_in, std_in = np.array(STATS[0:3], np.float32), np.array(STATS[3:6], np.float32)
+    x = ocnn.to_ncdhw(torch.as_tensor(((m - mean_in) / std_in).astype(np.float32), dtype=torch.float64))
+    t = ocnn.to_ncdhw((tgt - np.array(STATS[6:9])) / np.array(STATS[9:12]))
+    L_ref, g_ref = ocnn.loss_and_grad(torch.as_tensor(flat), x, t, rnd=ocnn.bf16_round)
+    assert abs(float(loss) - L_ref) <= 1e-3 * abs(L_ref)
+    g = grad.double().cpu().numpy()
+    assert rel_l2(g, g_ref.numpy()) <= 1e-2, rel_l2(g, g_ref.numpy())
+    # every layer's weights and biases, not just the largest
+    o = 0
+    for s in ocnn.param_shapes():
+        n = int(np.prod(s))
+        assert rel_l2(g[o:o + n], g_ref.numpy()[o:o + n]) <= 3e-2, (s, rel_l2(g[o:o + n], g_ref.numpy()[o:o + n]))
+        o += n
+
+
+def test_adam_step_matches_oracle():
+    shape = (3, 20, 24)
+    net, flat = _net(shape, 1)
+    net.set_normalizer(STATS)
+    m = _fields(shape, 1, 54)
+    tgt = np.random.default_rng(55).normal(size=(1,) + shape + (3,)) * 1e5
+    _, g = net.loss_grad(_dev(m)[0], _dev(tgt)[0])
+    p0 = net.get_params().double().cpu()
+    net.adam_step(1e-3, 1e-4)
+    p1 = net.get_params().double().cpu()
+    ref, _, _ = ocnn.adam_step(p0, g.double().cpu(), torch.zeros_like(p0), torch.zeros_like(p0), 1, 1e-3, 1e-4)
+    assert float((p1 - ref).abs().max()) <= 1e-6 * float(p0.abs().max())
+
+
+def test_training_reduces_loss_and_in_loop_fallback():
+    from paper_2602_12242_gb300.surrogate import Surrogate, make_dataset, normalizer_stats, run_in_loop, train
+    c = cfg_of(nx=32, ny=32, nz=4)
+    ctx = context(c)
+    M, H = make_dataset(ctx, 96, seed0=9000)
+    net = Surrogate(32, 32, 4, max_batch=16)
+    net.set_params(torch.as_tensor(ocnn.init_params(3), dtype=torch.float32))
+    net.set_normalizer(normalizer_stats(M, H))
+    losses = train(net, M, H, epochs=6, batch=16, lr=2e-3)
+    assert losses[-1] < 0.7 * losses[0], losses
+    assert all(b < a for a, b in zip(losses, losses[1:])), losses
+    # in-loop: a surrogate this small cannot reach 1e-2, so the judge falls back
+    m = M[0].clone()
+    res = run_in_loop(ctx, net, m, nsteps=6, dt=1e-14, judge_every=3, threshold=1e-2)
+    assert res["errors"] and res["fallback_step"] == 3
+    nrm = torch.linalg.vector_norm(m[..., :3], dim=-1)
+    assert float((nrm - 1).abs().max()) < 1e-5
+    # with a loose threshold the surrogate stays in charge
+    m2 = M[1].clone()
+    res2 = run_in_loop(ctx, net, m2, nsteps=6, dt=1e-14, judge_every=3, threshold=10.0)
+    assert res2["fallback_step"] is None and len(res2["errors"]) == 2
