@@ -1,0 +1,137 @@
+"""Reports of the method's patterns against the plain FP32 path on one GPU.
+
+  python -m paper_2602_12242_gb300.patterns [--pairs N] [--epochs E] [--insteps S] [--out FILE]
+
+learned: the conv-net surrogate trained on (m, H_demag) pairs from the FFT
+  path on the learned workload (64x64x4 cells, smooth textures); held-out
+  error, time per demag evaluation and per RK4 step against the FFT, and an
+  in-loop run with the FFT as judge (every --judge steps) and fallback (error
+  above 1e-2), with the drift of m against the FFT-only trajectory.
+adjoint: time of the recorded forward plus the reverse sweep against the
+  plain forward run for the adjoint workload (128x128x1, 2000 RK4 steps,
+  a checkpoint every 100).
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import inputs
+from .solver import Context, to_dev4
+from .surrogate import Surrogate, init_params, make_dataset, normalizer_stats, run_in_loop, time_demag, train
+
+
+def _rk_time(ctx, m, n, dt):
+    ctx.rk_step(m, 2, dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ctx.rk_step(m, n, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def learned_report(pairs, epochs, batch, insteps, judge, holdout=64, log=print):
+    cfg = dict(inputs.CONFIGS["learned"])
+    ctx = Context.from_config(cfg)
+    t0 = time.perf_counter()
+    M, H = make_dataset(ctx, pairs + holdout, seed0=inputs.SEEDS["learned"])
+    t_data = time.perf_counter() - t0
+    net = Surrogate(cfg["nx"], cfg["ny"], cfg["nz"], max_batch=batch)
+    net.set_params(torch.as_tensor(init_params(11)))
+    net.set_normalizer(normalizer_stats(M[:pairs], H[:pairs]))
+    pred0 = net.forward(M[pairs:pairs + 1][0])
+    err_untrained = L.mx_rel_l2(ctx.h, pred0, H[pairs])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(net, M[:pairs], H[:pairs], epochs=epochs, batch=batch, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    errs = []
+    for i in range(pairs, pairs + holdout):
+        errs.append(L.mx_rel_l2(ctx.h, net.forward(M[i]), H[i]))
+    m_test = M[pairs].clone()
+    tdem = time_demag(ctx, net, m_test)
+    # RK4 step time with each backend
+    m1 = M[pairs].clone()
+    t_fft = _rk_time(ctx, m1, 100, cfg["dt"])
+    L.mx_set_demag_surrogate(ctx.h, net.h)
+    m2 = M[pairs].clone()
+    t_sur = _rk_time(ctx, m2, 100, cfg["dt"])
+    L.mx_set_demag_surrogate(ctx.h, None)
+    # in-loop runs from a held-out texture
+    ref = M[pairs + 1].clone()
+    ctx.rk_step(ref, insteps, cfg["dt"])
+    judged = M[pairs + 1].clone()
+    res = run_in_loop(ctx, net, judged, insteps, cfg["dt"], judge, threshold=1e-2)
+    free = M[pairs + 1].clone()
+    res_free = run_in_loop(ctx, net, free, insteps, cfg["dt"], judge, threshold=float("inf"))
+    drift_free = float((free[..., :3] - ref[..., :3]).abs().max())
+    drift_judged = float((judged[..., :3] - ref[..., :3]).abs().max())
+    return {
+        "workload": "learned 64x64x4, smooth textures sigma 8 cells",
+        "pairs": pairs, "holdout": holdout, "epochs": epochs, "batch": batch,
+        "dataset_s": t_data, "train_s": t_train,
+        "train_samples_per_s": pairs * epochs / t_train,
+        "loss_first_last": [losses[0], losses[-1]],
+        "holdout_rel_l2_mean": float(np.mean(errs)), "holdout_rel_l2_max": float(np.max(errs)),
+        "untrained_rel_l2": err_untrained,
+        "demag_eval_ms": tdem, "rk4_step_ms": {"fft": t_fft, "surrogate": t_sur},
+        "in_loop": {"steps": insteps, "judge_every": judge, "threshold": 1e-2,
+                    "fallback_step": res["fallback_step"], "first_errors": res["errors"][:5],
+                    "free_run_errors": res_free["errors"][:: max(1, len(res_free["errors"]) // 10)],
+                    "max_drift_m_free_run": drift_free, "max_drift_m_judged_run": drift_judged},
+    }
+
+
+def adjoint_report(nsteps=2000, every=100):
+    cfg = dict(inputs.CONFIGS["adjoint"])
+    Ms, _, _ = inputs.material("adjoint")
+    ctx = Context.from_config(cfg, Ms=Ms)
+    m0 = to_dev4(inputs.initial_m("adjoint"))
+    m = m0.clone()
+    t_plain = _rk_time(ctx, m, nsteps, cfg["dt"]) * nsteps
+    ctx.adjoint_reserve(nsteps, every)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    mT = ctx.rk_forward_record(m0, cfg["dt"])
+    e1.record()
+    lam = torch.zeros_like(mT)
+    lam[:, 48:80, 48:80, 2] = 1.0 / (32 * 32)
+    g, gms = ctx.rk_backward(lam)
+    e2.record()
+    torch.cuda.synchronize()
+    return {"workload": "adjoint 128x128x1, 2000 RK4 steps, checkpoint every 100",
+            "plain_forward_ms": t_plain, "recorded_forward_ms": e0.elapsed_time(e1),
+            "backward_ms": e1.elapsed_time(e2),
+            "gradient_cost_over_plain_forward": e0.elapsed_time(e2) / t_plain,
+            "grad_m0_norm": float(g[..., :3].norm()), "grad_ms_norm": float(gms.norm())}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=100)
+    ap.add_argument("--batch", type=int, default=128)
+    ap.add_argument("--insteps", type=int, default=5000)
+    ap.add_argument("--judge", type=int, default=100)
+    ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    rep = {"learned": learned_report(a.pairs, a.epochs, a.batch, a.insteps, a.judge)}
+    if not a.skip_adjoint:
+        rep["adjoint"] = adjoint_report()
+    s = json.dumps(rep)
+    print(s, flush=True)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(s + "\n")
+
+
+if __name__ == "__main__":
+    main()

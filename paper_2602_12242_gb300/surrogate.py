@@ -16,6 +16,22 @@ from . import inputs
 from .solver import to_dev4
 
 
+CHANNELS = (3, 32, 64, 32, 3)
+
+
+def init_params(seed):
+    """Seeded initial parameters: each layer's weights and biases uniform in
+    +-1/sqrt(fan_in) (fan_in = 27 * input channels), in the library's order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for l in range(4):
+        cin, cout = CHANNELS[l], CHANNELS[l + 1]
+        bound = 1.0 / np.sqrt(cin * 27)
+        parts.append(rng.uniform(-bound, bound, size=cout * cin * 27))
+        parts.append(rng.uniform(-bound, bound, size=cout))
+    return np.concatenate(parts).astype(np.float32)
+
+
 class Surrogate:
     """The 3 -> 32 -> 64 -> 32 -> 3 conv net of libmx for one grid."""
 
