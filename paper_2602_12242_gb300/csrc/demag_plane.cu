@@ -102,21 +102,31 @@ __global__ void __launch_bounds__(3 * kRows * S, 2) xik_kernel(const float2* __r
   const int y0 = (blockIdx.x % ychunks) * kRows;
   const int tid = threadIdx.x;
   const long plane = 3L * g.nz * g.ny;
-  for (int e = tid; e < 3 * kRows * M; e += NT) {
-    const int r = e % kRows;
-    const int c = (e / kRows) % 3;
-    const int k = e / (3 * kRows);
-    const int y = y0 + r;
-    float2 v = make_float2(0.f, 0.f);
-    if (y < g.ny) {
-      const long o = ((long)c * g.nz + z) * g.ny + y;
-      const float2 a = __ldg(&w2[(long)k * plane + o]);
-      const float2 b = cconj(__ldg(&w2[(long)(M - k) * plane + o]));
+  constexpr int kB = 4;  // independent loads in flight per thread
+  for (int e0 = tid; e0 < 3 * kRows * M; e0 += NT * kB) {
+    float2 A[kB], Bv[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * NT;
+      const int r = e % kRows, c = (e / kRows) % 3, k = e / (3 * kRows);
+      const int y = y0 + r;
+      A[u] = Bv[u] = make_float2(0.f, 0.f);
+      if (e < 3 * kRows * M && y < g.ny) {
+        const long o = ((long)c * g.nz + z) * g.ny + y;
+        A[u] = __ldg(&w2[(long)k * plane + o]);
+        Bv[u] = __ldg(&w2[(long)(M - k) * plane + o]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * NT;
+      if (e >= 3 * kRows * M) break;
+      const int r = e % kRows, c = (e / kRows) % 3, k = e / (3 * kRows);
+      const float2 a = A[u], b = cconj(Bv[u]);
       const float2 Sv = cadd(a, b);
       const float2 t = cmul(cconj(__ldg(&twP[k])), csub(a, b));
-      v = make_float2(Sv.x - t.y, Sv.y + t.x);
+      sm[(3 * r + c) * P + k] = make_float2(Sv.x - t.y, Sv.y + t.x);
     }
-    sm[(3 * r + c) * P + k] = v;
   }
   __syncthreads();
   line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
@@ -159,18 +169,32 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
   const float* nk = nhk + (long)kx * 6 * g.Oz * g.Oy;
   const long cst = (long)g.Oz * g.Oy;
   float2* twZ = twS + LH;                         // W_P^(r n) for r < 4, n < 2Q
-  for (int q = tid; q < LH; q += NT) twS[q] = __ldg(&twH[q]);
+  float2* twS2 = twZ + 64;                        // W_Py^y, y < Py/2
+  for (int q = tid; q < LH; q += NT) {
+    twS[q] = __ldg(&twH[q]);
+    twS2[q] = __ldg(&twPy[q]);
+  }
   for (int q = tid; q < 8 * Q; q += NT) twZ[q] = __ldg(&twz[((q / (2 * Q)) * (q % (2 * Q))) % P]);
 
   for (int h = 0; h < 2; ++h) {
-    for (int e = tid; e < nlines * LH; e += NT) {
-      const int line = e / LH, y = e % LH;
-      float2 v = make_float2(0.f, 0.f);
-      if (y < ny) {
-        v = __ldg(&w1[kxoff + (long)line * ny + y]);
-        if (h) v = cmul(v, __ldg(&twPy[y]));
+    // batches of kB independent loads per thread keep many requests in flight
+    constexpr int kB = 4;
+    for (int e0 = tid; e0 < nlines * LH; e0 += NT * kB) {
+      float2 v[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int e = e0 + u * NT;
+        const int line = e / LH, y = e % LH;
+        v[u] = make_float2(0.f, 0.f);
+        if (e < nlines * LH && y < ny) v[u] = __ldg(&w1[kxoff + (long)line * ny + y]);
       }
-      sm[line * PITCH + y] = v;
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int e = e0 + u * NT;
+        if (e >= nlines * LH) break;
+        const int line = e / LH, y = e % LH;
+        sm[line * PITCH + y] = (h && y < ny) ? cmul(v[u], twS2[y]) : v[u];
+      }
     }
     __syncthreads();
     for (int l0 = 0; l0 < nlines; l0 += NT / S) {
@@ -257,15 +281,30 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
       line_fft<E, S, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
     }
     __syncthreads();
-    for (int e = tid; e < nlines * ny; e += NT) {
-      const int line = e / ny, y = e % ny;
-      float2 v = sm[line * PITCH + y];
-      const long o = kxoff + (long)line * ny + y;
-      if (h == 0) {
-        w2[o] = v;
-      } else {
-        v = cmul(v, cconj(__ldg(&twPy[y])));
-        w2[o] = cadd(w2[o], v);
+    if (h == 0) {
+      for (int e = tid; e < nlines * ny; e += NT) {
+        const int line = e / ny, y = e % ny;
+        w2[kxoff + (long)line * ny + y] = sm[line * PITCH + y];
+      }
+    } else {
+      for (int e0 = tid; e0 < nlines * ny; e0 += NT * kB) {
+        float2 prev[kB];
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const int e = e0 + u * NT;
+          if (e < nlines * ny) {
+            const int line = e / ny, y = e % ny;
+            prev[u] = w2[kxoff + (long)line * ny + y];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          const int e = e0 + u * NT;
+          if (e >= nlines * ny) break;
+          const int line = e / ny, y = e % ny;
+          const float2 v = cmul(sm[line * PITCH + y], cconj(twS2[y]));
+          w2[kxoff + (long)line * ny + y] = cadd(prev[u], v);
+        }
       }
     }
     __syncthreads();
@@ -277,7 +316,7 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
 // ---------------------------------------------------------------------------
 template <int E, int S> static size_t xk_smem() { return sizeof(float2) * 3 * kRows * (LineFft<E, S>::kPitch + 1); }
 template <int E, int S> static size_t yzh_smem(int nz) {
-  return sizeof(float2) * ((3 * nz + 1) * LineFft<E, S>::kPitch + E * S + 64);
+  return sizeof(float2) * ((3 * nz + 1) * LineFft<E, S>::kPitch + 2 * E * S + 64);
 }
 
 template <int E, int S>
