@@ -26,7 +26,7 @@
 namespace mx {
 
 constexpr int kRows = 8;      // rows per block in xfk / xik
-constexpr int kPlaneNT = 512; // threads per yzh block
+constexpr int kPlaneNT = 384; // threads per yzh block (48 lines of 16 threads in two passes)
 
 // ---------------------------------------------------------------------------
 // x forward into the kx-major spectrum.
@@ -209,6 +209,22 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
       const int ky = 2 * kyh + h;
       const bool fy = ky > (g.Py >> 1);
       const int qy = fy ? g.Py - ky : ky;
+      // tensor values of this lane's kz = 4q + r, loaded first so that they
+      // arrive while the forward z FFTs run
+      float tn[Q][6];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int kz = 4 * q + r;
+        const bool fz = kz > (P >> 1);
+        const int qz = fz ? P - kz : kz;
+        const long o = (long)qz * g.Oy + qy;
+        tn[q][0] = __ldg(&nk[o]);
+        tn[q][1] = __ldg(&nk[cst + o]);
+        tn[q][2] = __ldg(&nk[2 * cst + o]);
+        tn[q][3] = (fy ? -1.f : 1.f) * __ldg(&nk[3 * cst + o]);
+        tn[q][4] = (fz ? -1.f : 1.f) * __ldg(&nk[4 * cst + o]);
+        tn[q][5] = ((fy != fz) ? -1.f : 1.f) * __ldg(&nk[5 * cst + o]);
+      }
       float2 Z[3][Q];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -224,14 +240,8 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
       for (int c = 0; c < 3; ++c) RegFft<Q, false>::run(Z[c]);
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const int kz = 4 * q + r;
-        const bool fz = kz > (P >> 1);
-        const int qz = fz ? P - kz : kz;
-        const long o = (long)qz * g.Oy + qy;
-        const float nxx = __ldg(&nk[o]), nyy = __ldg(&nk[cst + o]), nzz = __ldg(&nk[2 * cst + o]);
-        const float nxy = (fy ? -1.f : 1.f) * __ldg(&nk[3 * cst + o]);
-        const float nxz = (fz ? -1.f : 1.f) * __ldg(&nk[4 * cst + o]);
-        const float nyz = ((fy != fz) ? -1.f : 1.f) * __ldg(&nk[5 * cst + o]);
+        const float nxx = tn[q][0], nyy = tn[q][1], nzz = tn[q][2];
+        const float nxy = tn[q][3], nxz = tn[q][4], nyz = tn[q][5];
         const float2 mx = Z[0][q], my = Z[1][q], mz = Z[2][q];
         Z[0][q] = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
         Z[1][q] = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
