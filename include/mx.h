@@ -72,6 +72,12 @@ typedef enum {
  *           MX_DEMAG_GENERIC forces the size-generic separate passes;
  *           MX_DEMAG_PLANE forces the per-kx-plane kernel (MX_ERR_UNSUPPORTED
  *           at mx_create if the grid does not fit it)
+ *   fft_mode  MX_FFT_FP32 (default): every FFT stage in FP32 on the CUDA
+ *           cores; MX_FFT_SPLIT_BF16: the first radix-32 stage of the x
+ *           transforms runs as a DFT-as-GEMM on the tensor cores with operands
+ *           split into BF16 hi + lo parts (three products, FP32 accumulation),
+ *           relative error near 2^-16 per stage; needs the per-kx-plane path
+ *           and Px/2 in {512, 1024} (MX_ERR_UNSUPPORTED otherwise)
  */
 typedef struct {
     int nx, ny, nz;
@@ -83,10 +89,14 @@ typedef struct {
     int precession;
     int demag;
     int demag_path;
+    int fft_mode;
 } mx_params;
 
 /* Demag convolution schedules for mx_params.demag_path. */
 enum { MX_DEMAG_AUTO = 0, MX_DEMAG_GENERIC = 1, MX_DEMAG_PLANE = 2 };
+
+/* Arithmetic of the demag FFT stages for mx_params.fft_mode. */
+enum { MX_FFT_FP32 = 0, MX_FFT_SPLIT_BF16 = 1 };
 
 /* Field terms, for mx_heff's term mask. */
 enum {

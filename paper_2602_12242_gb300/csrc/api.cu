@@ -181,6 +181,10 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
     set_error("mx_create: demag_path must be MX_DEMAG_AUTO, MX_DEMAG_GENERIC or MX_DEMAG_PLANE");
     return MX_ERR_INVALID_ARG;
   }
+  if (p->fft_mode != MX_FFT_FP32 && p->fft_mode != MX_FFT_SPLIT_BF16) {
+    set_error("mx_create: fft_mode must be MX_FFT_FP32 or MX_FFT_SPLIT_BF16");
+    return MX_ERR_INVALID_ARG;
+  }
   if (p->dmi_interfacial && p->D != 0.0 && !(p->A > 0)) {
     set_error("mx_create: DMI boundary condition needs A > 0");
     return MX_ERR_INVALID_ARG;
@@ -262,7 +266,7 @@ mx_status mx_destroy(mx_ctx* ctx) {
   invalidate_graph(ctx);
   adjoint_free(ctx);
   void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_yh, ctx->tw_y,
-                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered, ctx->red2};
+                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered, ctx->red2, ctx->dft_a};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);

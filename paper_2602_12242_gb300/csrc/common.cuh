@@ -124,6 +124,7 @@ struct mx_ctx {
   float2* tw_m = nullptr;         // W_M^k, k < M = Px/2
   float2* tw_yh = nullptr;        // W_{Py/2}^k, k < Py/2
   bool plane = false;             // per-kx plane kernel (kx-major spectra and tensor)
+  void* dft_a = nullptr;          // split-BF16 DFT matrices (MX_FFT_SPLIT_BF16)
   int yz_tile = 1;                // kx columns per block in the fused kernel
   double* t_real = nullptr;       // FP64 real-space tensor octant (kept for checking)
   double spectrum_imag_ratio = 0; // max|Im| / max|Re| of the FP64 tensor spectrum

@@ -407,13 +407,22 @@ mx_status plane_setup(mx_ctx* ctx) {
     set_error("mx_create: the per-kx plane demag kernel does not support this grid");
     return MX_ERR_UNSUPPORTED;
   }
+  if (ctx->p.fft_mode == MX_FFT_SPLIT_BF16) {
+    if (!ctx->plane) {
+      set_error("mx_create: MX_FFT_SPLIT_BF16 needs the per-kx plane demag path");
+      return MX_ERR_UNSUPPORTED;
+    }
+    MX_TRY(dft_x_pass(ctx, nullptr, nullptr, false, nullptr, true));
+    MX_TRY(dft_gemm_setup(ctx));
+  }
   return MX_OK;
 }
 
 mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st) {
+  const bool dft = ctx->p.fft_mode == MX_FFT_SPLIT_BF16;
   {
     ProfScope ps(ctx, KID_X_FWD, st);
-    MX_TRY(xk_pass(ctx, m, nullptr, false, st, false));
+    MX_TRY(dft ? dft_x_pass(ctx, m, nullptr, false, st, false) : xk_pass(ctx, m, nullptr, false, st, false));
   }
   {
     ProfScope ps(ctx, KID_YZ, st);
@@ -421,7 +430,7 @@ mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
   }
   {
     ProfScope ps(ctx, KID_X_INV, st);
-    MX_TRY(xk_pass(ctx, nullptr, hd, true, st, false));
+    MX_TRY(dft ? dft_x_pass(ctx, nullptr, hd, true, st, false) : xk_pass(ctx, nullptr, hd, true, st, false));
   }
   return MX_OK;
 }

@@ -47,6 +47,10 @@ mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 mx_status cnn_demag(struct mx_cnn* n, const float4* m, float4* h, cudaStream_t st);
 bool cnn_matches(const struct mx_cnn* n, const Grid& g);
 
+// dftgemm.cu
+mx_status dft_gemm_setup(mx_ctx* ctx);
+mx_status dft_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup);
+
 // newell.cu
 mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st);
 

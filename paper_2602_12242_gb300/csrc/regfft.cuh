@@ -80,6 +80,30 @@ template <int E, int S> struct LineFft {
 
 // In-place FFT of `line` (natural order in and out).  `s` in [0, S); the S
 // threads of a line are consecutive lanes of one warp.  twL[q] = W_L^q.
+// Second step of line_fft: the twiddled E x S matrix is in rows k1 * (S + 1);
+// thread s does S-point FFTs over s for k1 = s + S j and writes X[k1 + E k2]
+// in natural order.
+template <int E, int S, bool INV>
+__device__ __forceinline__ void line_fft_step2(float2* line, int s) {
+  float2 v[E];
+  constexpr int J = E / S;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int k1 = s + S * j;
+#pragma unroll
+    for (int t = 0; t < S; ++t) v[j * S + t] = line[k1 * (S + 1) + t];
+    RegFft<S, INV>::run(&v[j * S]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int k1 = s + S * j;
+#pragma unroll
+    for (int t = 0; t < S; ++t) line[k1 + E * t] = v[j * S + t];
+  }
+  __syncwarp();
+}
+
 template <int E, int S, bool INV, bool TW_SHARED = false>
 __device__ __forceinline__ void line_fft(float2* line, int s, const float2* __restrict__ twL) {
   static_assert(E >= S && (E % S) == 0 && S <= 32, "line_fft shape");
@@ -103,22 +127,7 @@ __device__ __forceinline__ void line_fft(float2* line, int s, const float2* __re
 #pragma unroll
   for (int k = 0; k < E; ++k) line[k * (S + 1) + s] = v[k];
   __syncwarp();
-  constexpr int J = E / S;
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int k1 = s + S * j;
-#pragma unroll
-    for (int t = 0; t < S; ++t) v[j * S + t] = line[k1 * (S + 1) + t];
-    RegFft<S, INV>::run(&v[j * S]);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const int k1 = s + S * j;
-#pragma unroll
-    for (int t = 0; t < S; ++t) line[k1 + E * t] = v[j * S + t];
-  }
-  __syncwarp();
+  line_fft_step2<E, S, INV>(line, s);
 }
 
 }  // namespace mx

@@ -27,7 +27,7 @@ class Context:
 
     def __init__(self, nx, ny, nz, dx, dy, dz, Ms=8e5, A=1.3e-11, Ku=0.0, D=0.0, alpha=0.5,
                  gamma=2.211e5, ku_axis=(0.0, 0.0, 1.0), h_bias=(0.0, 0.0, 0.0), dmi=False,
-                 precession=True, demag=True, demag_path=0, build=True, stream=None):
+                 precession=True, demag=True, demag_path=0, fft_mode=0, build=True, stream=None):
         p = L.mx_params()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
         p.dx, p.dy, p.dz = float(dx), float(dy), float(dz)
@@ -37,6 +37,7 @@ class Context:
         p.h_bias[:] = [float(v) for v in h_bias]
         p.dmi_interfacial, p.precession, p.demag = int(bool(dmi)), int(bool(precession)), int(bool(demag))
         p.demag_path = int(demag_path)
+        p.fft_mode = int(fft_mode)
         self.params = p
         self.shape = (int(nz), int(ny), int(nx))
         self.h = None

@@ -36,6 +36,34 @@ def test_bulk_demag_field_precision():
     assert e_full <= 1e-5 and e_crop <= 1e-5
 
 
+def test_split_bf16_dft_stage_error():
+    """The optional split-BF16 DFT-as-GEMM first stage of the x transforms
+    (tensor cores): its demag field against the FP64 oracle, on a ragged grid
+    and on the full bulk grid.  Expected error near 2^-16 relative per GEMM
+    stage; bound 1e-4 (looser than the FP32 path's 1e-5, stated not gated)."""
+    from paper_2602_12242_gb300 import MX_TERM_DEMAG, MxError, _lib, inputs
+    from paper_2602_12242_gb300.solver import from_dev4, to_dev4
+    from helpers import cfg_of, random_m
+    c = cfg_of(nx=300, ny=40, nz=3, dx=2.5e-9, dy=2e-9, dz=3e-9)
+    m = f32(random_m(c, 91))
+    ctx = context(c, demag_path=_lib.MX_DEMAG_PLANE, fft_mode=_lib.MX_FFT_SPLIT_BF16)
+    ref = mm.demag_field(problem(c), t64(m)).numpy()
+    e_small = rel_l2(from_dev4(ctx.heff(to_dev4(m), terms=MX_TERM_DEMAG)), ref)
+    cb = dict(inputs.CONFIGS["bulk"])
+    mb = f32(inputs.initial_m("bulk"))
+    _, _, axis = inputs.material("bulk")
+    ctxb = context(cb, axis=f32(axis), fft_mode=_lib.MX_FFT_SPLIT_BF16)
+    Hb = from_dev4(ctxb.heff(to_dev4(mb), terms=MX_TERM_DEMAG))
+    refb = mm.demag_field(problem(cb, axis=f32(axis)), t64(mb)).numpy()
+    e_bulk = rel_l2(Hb, refb)
+    print(f"\nsplit-BF16 DFT stage: H_demag rel L2 vs FP64 {e_small:.2e} (300x40x3), {e_bulk:.2e} (bulk)")
+    assert e_small <= 1e-4 and e_bulk <= 1e-4
+    # grids outside the mode's reach are refused at creation
+    with pytest.raises(MxError) as ei:
+        context(cfg_of(nx=32, ny=32, nz=4), fft_mode=_lib.MX_FFT_SPLIT_BF16)
+    assert ei.value.status == _lib.MX_ERR_UNSUPPORTED
+
+
 def test_bulk_crop_trajectory_and_energy_precision():
     from paper_2602_12242_gb300 import inputs
     from paper_2602_12242_gb300.solver import from_dev4, to_dev4
