@@ -84,3 +84,19 @@ def central_fd(p, m0_raw, dt, nsteps, objective, direction_m=None, direction_ms=
     jp = objective_value(p, m0 + h * dm, dt, nsteps, objective, Ms + h * ds)
     jm = objective_value(p, m0 - h * dm, dt, nsteps, objective, Ms - h * ds)
     return (jp - jm) / (2 * h)
+
+
+def tangent_linear(p, m0_raw, dt, nsteps, dm0, dms=None):
+    """Tangent-linear model: the directional derivative of m_nsteps along
+    (dm0 in m0_raw, dms in Ms), by forward-mode differentiation of the same
+    discrete forward map (independent of the reverse sweep in ``gradient``)."""
+    import torch.autograd.forward_ad as fwd
+    m0_raw = mm.as_t(m0_raw).detach()
+    Ms = mm.ms_field(p).detach().clone()
+    dms = torch.zeros_like(Ms) if dms is None else mm.as_t(dms)
+    with fwd.dual_level():
+        q = _with_ms(p, fwd.make_dual(Ms, dms))
+        m = mm.normalize(fwd.make_dual(m0_raw, mm.as_t(dm0)))
+        for _ in range(nsteps):
+            m = mm.rk4_step(q, m, dt)
+        return fwd.unpack_dual(m).tangent.detach()

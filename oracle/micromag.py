@@ -148,8 +148,22 @@ class _DemagOp(torch.autograd.Function):
     def forward(ctx, m, Ms, p):
         ctx.p = p
         ctx.save_for_backward(m, Ms)
+        ctx.save_for_forward(m, Ms)
         M = (Ms[..., None] * m).detach().numpy()
         return torch.from_numpy(_convolve(p, M))
+
+    @staticmethod
+    def jvp(ctx, m_t, Ms_t, p_t):
+        """Tangent (forward mode, used by the tangent-linear check of the
+        adjoint): the operator is linear in Ms m, so the tangent is the same
+        convolution of Ms dm + dMs m; no symmetry of N is assumed."""
+        m, Ms = ctx.saved_tensors
+        src = torch.zeros_like(m)
+        if m_t is not None:
+            src = src + Ms[..., None] * m_t
+        if Ms_t is not None:
+            src = src + Ms_t[..., None] * m
+        return torch.from_numpy(_convolve(ctx.p, src.detach().numpy()))
 
     @staticmethod
     def backward(ctx, g):

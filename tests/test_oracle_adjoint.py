@@ -50,3 +50,19 @@ def test_gradient_is_tangent_to_the_initial_normalisation(setup):
     p, m0, obj, J, g_m, g_ms, rng = setup
     dots = (g_m * torch.from_numpy(m0)).sum(-1)
     assert float(dots.abs().max()) <= 1e-12 * float(g_m.abs().max()) * np.abs(m0).max()
+
+
+def test_dot_product_tangent_linear_vs_adjoint(setup):
+    """<TLM d, w> = <d, ADJ w> for random d (in m0 and Ms) and w: the
+    forward-mode tangent of the run and the step-wise reverse sweep are two
+    independent derivatives of the same discrete map."""
+    p, m0, obj, J, g_m, g_ms, rng = setup
+    for _ in range(2):
+        w = torch.from_numpy(rng.normal(size=m0.shape))
+        dm = rng.normal(size=m0.shape)
+        ds = rng.normal(size=(1, 8, 10)) * 1e4
+        _, gw_m, gw_ms = adj.gradient(p, m0, 2e-14, 12, lambda m: (m * w).sum())
+        tl = adj.tangent_linear(p, m0, 2e-14, 12, dm, ds)
+        lhs = float((tl * w).sum())
+        rhs = float((gw_m * torch.from_numpy(dm)).sum() + (gw_ms * torch.from_numpy(ds)).sum())
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
