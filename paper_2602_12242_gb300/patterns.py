@@ -10,6 +10,11 @@ learned: the conv-net surrogate trained on (m, H_demag) pairs from the FFT
 adjoint: time of the recorded forward plus the reverse sweep against the
   plain forward run for the adjoint workload (128x128x1, 2000 RK4 steps,
   a checkpoint every 100).
+
+  python -m paper_2602_12242_gb300.patterns --trajectory film --steps 20000 --every 1000 --npz FILE
+
+trajectory: snapshots of m every --every RK4 steps of a workload from its
+  seeded initial state (for the FP32-vs-FP64 divergence curve).
 """
 import argparse
 import json
@@ -113,8 +118,32 @@ def adjoint_report(nsteps=2000, every=100):
             "grad_m0_norm": float(g[..., :3].norm()), "grad_ms_norm": float(gms.norm())}
 
 
+def trajectory(name, steps, every):
+    """m (float32, (n_snap, nz, ny, nx, 3)) at steps 0, every, 2 every, ... of
+    a workload's RK4 run from its seeded initial state, and those step counts."""
+    cfg = dict(inputs.CONFIGS[name])
+    Ms, Ku, axis = inputs.material(name)
+    ctx = Context.from_config(cfg, Ms=Ms, Ku=Ku, ku_axis=axis)
+    m = to_dev4(inputs.initial_m(name))
+    snaps, at = [m[..., :3].cpu().numpy().copy()], [0]
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        ctx.rk_step(m, k, cfg["dt"])
+        done += k
+        snaps.append(m[..., :3].cpu().numpy().copy())
+        at.append(done)
+    ctx.sync()
+    ctx.close()
+    return np.stack(snaps), np.array(at)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--trajectory", default=None, choices=list(inputs.CONFIGS))
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--every", type=int, default=1000)
+    ap.add_argument("--npz", default=None)
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--batch", type=int, default=128)
@@ -123,6 +152,10 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    if a.trajectory:
+        snaps, at = trajectory(a.trajectory, a.steps, a.every)
+        np.savez_compressed(a.npz or f"{a.trajectory}_fp32.npz", m=snaps, step=at)
+        return
     rep = {"learned": learned_report(a.pairs, a.epochs, a.batch, a.insteps, a.judge)}
     if not a.skip_adjoint:
         rep["adjoint"] = adjoint_report()
