@@ -207,7 +207,9 @@ mx_status mx_energy_noalloc(const mx_params *p, const float *m, const float *h_d
                             double *e_out, mx_stream_t stream);
 
 /* Synchronise `stream`; return MX_ERR_NONFINITE (and clear the flag) if any
- * kernel of this context produced a NaN or Inf since the last mx_sync. */
+ * kernel of this context produced a NaN or Inf since the last mx_sync, or
+ * MX_ERR_TIMEOUT if a bounded wait for a bulk copy in the demag kernel ran out
+ * (its results are then invalid). */
 mx_status mx_sync(mx_ctx *ctx, mx_stream_t stream);
 
 /* Padded grid of this context: out[0..2] = Px, Py, Pz. */

@@ -213,7 +213,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
     }
   };
   const long no = (long)g.Hx * g.Oy * g.Oz;
-  alloc((void**)&ctx->nhat, sizeof(float) * 6 * no);
+  alloc((void**)&ctx->nhat, sizeof(float) * (6 * no > plane_octant_size(g) ? 6 * no : plane_octant_size(g)));
   alloc((void**)&ctx->w1, sizeof(float2) * 3 * (long)g.nz * g.ny * g.Hx);
   alloc((void**)&ctx->tw_x, sizeof(float2) * g.Px);
   alloc((void**)&ctx->tw_m, sizeof(float2) * (g.Px > 1 ? g.Px / 2 : 1));
@@ -265,7 +265,7 @@ mx_status mx_destroy(mx_ctx* ctx) {
   if (!ctx) return MX_OK;
   invalidate_graph(ctx);
   adjoint_free(ctx);
-  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_yh, ctx->tw_y,
+  void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_mk, ctx->tw_yh, ctx->tw_y,
                   ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered, ctx->red2, ctx->dft_a};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -504,6 +504,10 @@ mx_status mx_sync(mx_ctx* ctx, mx_stream_t stream) {
   if (flag) {
     MX_CUDA_TRY(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st));
     MX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flag & kFlagTimeout) {
+      set_error("mx_sync: a bounded wait for a bulk copy in the demag kernel ran out");
+      return MX_ERR_TIMEOUT;
+    }
     set_error("mx_sync: a kernel produced a non-finite value");
     return MX_ERR_NONFINITE;
   }

@@ -69,6 +69,10 @@ template <bool INV, typename C> __device__ __forceinline__ C cmul_mi(C a) {
 // ---------------------------------------------------------------------------
 // Derived per-context constants passed to kernels by value.
 // ---------------------------------------------------------------------------
+// Bits of the context's device status flag (read and cleared by mx_sync).
+constexpr int kFlagNonfinite = 1;  // a kernel produced a non-finite value
+constexpr int kFlagTimeout = 2;    // a bounded wait on a bulk copy ran out
+
 struct Grid {
   int nx, ny, nz;      // cells
   int Px, Py, Pz;      // padded lengths
@@ -76,6 +80,17 @@ struct Grid {
   int Oy, Oz;          // Py/2 + 1, Pz/2 + 1 (octant extents of the spectrum)
   long ncell;
 };
+
+// Tensor octant layout of the per-kx plane path: [kx][qz][qy mod 2][qy / 2][comp]
+// (6 comps innermost; qy split by parity so that the even-ky and odd-ky halves
+// of a plane each read contiguous rows, three float2 loads per (qz, qy)).
+__host__ __device__ __forceinline__ long plane_octant_index(const Grid& g, int kx, int comp, int qz, int qy) {
+  const int oyh = (g.Oy + 1) >> 1;
+  return ((((long)kx * g.Oz + qz) * 2 + (qy & 1)) * oyh + (qy >> 1)) * 6 + comp;
+}
+__host__ __device__ __forceinline__ long plane_octant_size(const Grid& g) {
+  return (long)g.Hx * g.Oz * 2 * ((g.Oy + 1) >> 1) * 6;
+}
 
 struct LocalCoef {
   float inv_dx2, inv_dy2, inv_dz2;   // 1/h^2
@@ -113,7 +128,7 @@ struct mx_ctx {
 
   // demag
   bool built = false;
-  float* nhat = nullptr;          // 6 x Oz x Oy x Hx
+  float* nhat = nullptr;          // tensor octant: [comp][qz][qy][kx], or plane_octant_index() on the plane path
   float2* w1 = nullptr;           // 3 x nz x ny x Hx   (after the x pass)
   float2* w2 = nullptr;           // 3 x nz x Py x Hx   (after the y pass; unfused path)
   float2* tw_x = nullptr;         // W_Px^k, k < Px
@@ -122,6 +137,7 @@ struct mx_ctx {
   bool fused_yz = false;          // y/z passes in one kernel (plane fits on chip)
   bool fast_x = false;            // compile-time-sized x passes available
   float2* tw_m = nullptr;         // W_M^k, k < M = Px/2
+  float2* tw_mk = nullptr;        // W_M^(s k) at [k * S + s] for the plane path's x line FFTs (M = E S)
   float2* tw_yh = nullptr;        // W_{Py/2}^k, k < Py/2
   bool plane = false;             // per-kx plane kernel (kx-major spectra and tensor)
   void* dft_a = nullptr;          // split-BF16 DFT matrices (MX_FFT_SPLIT_BF16)

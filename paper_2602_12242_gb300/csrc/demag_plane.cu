@@ -3,7 +3,8 @@
 // same as demag.cu, only the schedule differs).
 //
 // Spectra use a kx-major layout, w[kx][c][z][y] (y fastest), so a kx plane is
-// contiguous.  The tensor octant is stored the same way, nhat[kx][comp][qz][qy].
+// contiguous.  The tensor octant is kx-major too, [kx][qz][qy mod 2][qy / 2][comp]
+// (plane_octant_index).
 //
 //   xfk  r2c along x for R consecutive rows (same z); the spectrum is
 //        transposed in shared memory so the kx-major stores are coalesced.
@@ -18,15 +19,28 @@
 //        halves' inverses, the odd one times W_Py^-y: the even half is stored
 //        and the odd half is added to it.
 //   xik  c2r along x for R consecutive rows, reading the kx-major spectrum.
+#include <math.h>
+
+#include <vector>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "bulk.cuh"
 #include "regfft.cuh"
 
 namespace mx {
 
 constexpr int kRows = 8;      // rows per block in xfk / xik
 constexpr int kPlaneNT = 384; // threads per yzh block (48 lines of 16 threads in two passes)
+
+// Line pitch of the yzh plane in float2: the line FFT's footprint plus 2, so
+// that the pitch in 4-byte words is 4 mod 8 and the z stage's four lanes per
+// column (rows n, n + Q/2, n + Q, n + 3Q/2) write to two bank halves instead
+// of one.
+template <int E, int S> struct YzhPitch {
+  static constexpr int value = LineFft<E, S>::kPitch + 2;
+};
 
 // ---------------------------------------------------------------------------
 // x forward into the kx-major spectrum.
@@ -67,7 +81,7 @@ __global__ void __launch_bounds__(3 * kRows * S, 2) xfk_kernel(const float4* __r
     sm[(3 * r + 2) * P + n] = zz;
   }
   __syncthreads();
-  line_fft<E, S, false>(sm + (tid / S) * P, tid % S, twM);
+  line_fft<E, S, false, false, true>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
   const long plane = 3L * g.nz * g.ny;  // one kx
   for (int e = tid; e < 3 * kRows * (M + 1); e += NT) {
@@ -129,7 +143,7 @@ __global__ void __launch_bounds__(3 * kRows * S, 2) xik_kernel(const float2* __r
     }
   }
   __syncthreads();
-  line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
+  line_fft<E, S, true, false, true>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
   for (int e = tid; e < kRows * g.nx; e += NT) {
     const int r = e / g.nx, i = e % g.nx;
@@ -153,32 +167,64 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
                                                           Grid g, const float* __restrict__ nhk,
                                                           const float2* __restrict__ twPy,
                                                           const float2* __restrict__ twH,
-                                                          const float2* __restrict__ twz) {
+                                                          const float2* __restrict__ twz, int* flag) {
   constexpr int LH = E * S;                       // Py / 2
-  constexpr int PITCH = LineFft<E, S>::kPitch;
+  constexpr int PITCH = YzhPitch<E, S>::value;
   constexpr int Q = P / 4;                        // points per residue class of kz
   constexpr int NT = kPlaneNT;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
+  __shared__ __align__(8) uint64_t bar;           // completion of the bulk plane loads
   const int kx = blockIdx.x;
   const int tid = threadIdx.x;
   const int nz = g.nz, ny = g.ny;
   const int nlines = 3 * nz;
   const long kxoff = (long)kx * nlines * ny;
   float2* dummy = sm + nlines * PITCH;            // scratch line for idle groups
-  float2* twS = dummy + PITCH;                    // W_LH^q, q < LH, in shared memory
-  const float* nk = nhk + (long)kx * 6 * g.Oz * g.Oy;
-  const long cst = (long)g.Oz * g.Oy;
+  float2* twS = dummy + PITCH;                    // W_LH^(s k) at [k S + s], in shared memory
+  const int oyh = (g.Oy + 1) >> 1;
+  const float* nk = nhk + plane_octant_index(g, kx, 0, 0, 0);
   float2* twZ = twS + LH;                         // W_P^(r n) for r < 4, n < 2Q
   float2* twS2 = twZ + 64;                        // W_Py^y, y < Py/2
   for (int q = tid; q < LH; q += NT) {
-    twS[q] = __ldg(&twH[q]);
+    twS[q] = __ldg(&twH[(q % S) * (q / S)]);  // (S - 1)(E - 1) < LH
     twS2[q] = __ldg(&twPy[q]);
   }
   for (int q = tid; q < 8 * Q; q += NT) twZ[q] = __ldg(&twz[((q / (2 * Q)) * (q % (2 * Q))) % P]);
+  // Rows of w1/w2 are ny float2 at 8 ny-byte strides: with ny even every row
+  // starts on a 16-byte boundary and has a 16-byte multiple size, so the plane
+  // moves by bulk copies (one per row); the line pitch keeps the shared rows
+  // 16-byte aligned too.  Odd ny takes the per-element path.
+  const bool bulk = (ny & 1) == 0;
+  const uint32_t row_bytes = (uint32_t)ny * sizeof(float2);
+  uint32_t parity = 0;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
 
   for (int h = 0; h < 2; ++h) {
-    // batches of kB independent loads per thread keep many requests in flight
     constexpr int kB = 4;
+    if (bulk) {
+      fence_proxy_async_smem();
+      __syncthreads();  // the previous phase's shared-memory accesses are done
+      if (tid == 0) {
+        bulk_wait_read_all();  // the h = 0 bulk stores have read their rows
+        mbar_arrive_expect_tx(&bar, (uint32_t)nlines * row_bytes);
+        for (int line = 0; line < nlines; ++line)
+          bulk_load(sm + line * PITCH, w1 + kxoff + (long)line * ny, row_bytes, &bar);
+      }
+      for (int e = tid; e < nlines * (LH - ny); e += NT) {
+        const int line = e / (LH - ny), y = ny + e % (LH - ny);
+        sm[line * PITCH + y] = make_float2(0.f, 0.f);
+      }
+      if (!mbar_wait(&bar, parity)) atomicOr(flag, kFlagTimeout);
+      parity ^= 1;
+      if (h) {
+        for (int e = tid; e < nlines * ny; e += NT) {
+          const int line = e / ny, y = e % ny;
+          sm[line * PITCH + y] = cmul(sm[line * PITCH + y], twS2[y]);
+        }
+      }
+    } else
+    // batches of kB independent loads per thread keep many requests in flight
     for (int e0 = tid; e0 < nlines * LH; e0 += NT * kB) {
       float2 v[kB];
 #pragma unroll
@@ -199,7 +245,7 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
     __syncthreads();
     for (int l0 = 0; l0 < nlines; l0 += NT / S) {
       const int l = l0 + tid / S;
-      line_fft<E, S, false, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
+      line_fft<E, S, false, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
     }
     __syncthreads();
     // z stage: 4 lanes per ky column, lane r owns kz = 4q + r
@@ -217,13 +263,15 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
         const int kz = 4 * q + r;
         const bool fz = kz > (P >> 1);
         const int qz = fz ? P - kz : kz;
-        const long o = (long)qz * g.Oy + qy;
-        tn[q][0] = __ldg(&nk[o]);
-        tn[q][1] = __ldg(&nk[cst + o]);
-        tn[q][2] = __ldg(&nk[2 * cst + o]);
-        tn[q][3] = (fy ? -1.f : 1.f) * __ldg(&nk[3 * cst + o]);
-        tn[q][4] = (fz ? -1.f : 1.f) * __ldg(&nk[4 * cst + o]);
-        tn[q][5] = ((fy != fz) ? -1.f : 1.f) * __ldg(&nk[5 * cst + o]);
+        // the six components of (qz, qy) are contiguous (8-byte aligned)
+        const float2* t = reinterpret_cast<const float2*>(nk + (((long)qz * 2 + h) * oyh + (qy >> 1)) * 6);
+        const float2 t01 = __ldg(t), t23 = __ldg(t + 1), t45 = __ldg(t + 2);
+        tn[q][0] = t01.x;
+        tn[q][1] = t01.y;
+        tn[q][2] = t23.x;
+        tn[q][3] = fy ? -t23.y : t23.y;
+        tn[q][4] = fz ? -t45.x : t45.x;
+        tn[q][5] = (fy != fz) ? -t45.y : t45.y;
       }
       float2 Z[3][Q];
 #pragma unroll
@@ -288,15 +336,27 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
     __syncthreads();
     for (int l0 = 0; l0 < nlines; l0 += NT / S) {
       const int l = l0 + tid / S;
-      line_fft<E, S, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
+      line_fft<E, S, true, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
     }
     __syncthreads();
     if (h == 0) {
-      for (int e = tid; e < nlines * ny; e += NT) {
-        const int line = e / ny, y = e % ny;
-        w2[kxoff + (long)line * ny + y] = sm[line * PITCH + y];
+      if (bulk) {
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          for (int line = 0; line < nlines; ++line)
+            bulk_store(w2 + kxoff + (long)line * ny, sm + line * PITCH, row_bytes);
+          bulk_commit();
+        }
+      } else {
+        for (int e = tid; e < nlines * ny; e += NT) {
+          const int line = e / ny, y = e % ny;
+          w2[kxoff + (long)line * ny + y] = sm[line * PITCH + y];
+        }
       }
     } else {
+      if (bulk && tid == 0) bulk_wait_all();  // the h = 0 rows are in w2
+      __syncthreads();
       for (int e0 = tid; e0 < nlines * ny; e0 += NT * kB) {
         float2 prev[kB];
 #pragma unroll
@@ -326,7 +386,7 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
 // ---------------------------------------------------------------------------
 template <int E, int S> static size_t xk_smem() { return sizeof(float2) * 3 * kRows * (LineFft<E, S>::kPitch + 1); }
 template <int E, int S> static size_t yzh_smem(int nz) {
-  return sizeof(float2) * ((3 * nz + 1) * LineFft<E, S>::kPitch + 2 * E * S + 64);
+  return sizeof(float2) * ((3 * nz + 1) * YzhPitch<E, S>::value + 2 * E * S + 64);
 }
 
 template <int E, int S>
@@ -335,16 +395,25 @@ static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
   if (setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(xfk_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     MX_CUDA_TRY(cudaFuncSetAttribute(xik_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    constexpr int M = E * S;
+    std::vector<float2> t(M);
+    for (int k = 0; k < E; ++k)
+      for (int s = 0; s < S; ++s) {
+        const double a = -2.0 * kPi * (double)(s * k) / (double)M;
+        t[k * S + s] = make_float2((float)cos(a), (float)sin(a));
+      }
+    if (!ctx->tw_mk) MX_CUDA_TRY(cudaMalloc(&ctx->tw_mk, sizeof(float2) * M));
+    MX_CUDA_TRY(cudaMemcpy(ctx->tw_mk, t.data(), sizeof(float2) * M, cudaMemcpyHostToDevice));
     return MX_OK;
   }
   const Grid& g = ctx->g;
   const int nblk = g.nz * ((g.ny + kRows - 1) / kRows);
   if (!inverse) {
-    xfk_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, ctx->tw_m,
+    xfk_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, ctx->tw_mk,
                                                        ctx->tw_x);
     return launch_check("xfk_kernel");
   }
-  xik_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(ctx->w2, g, hd, ctx->tw_m, ctx->tw_x);
+  xik_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(ctx->w2, g, hd, ctx->tw_mk, ctx->tw_x);
   return launch_check("xik_kernel");
 }
 
@@ -357,7 +426,8 @@ static mx_status yzh_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(yzh_kernel<E, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
-  yzh_kernel<E, S, P><<<g.Hx, kPlaneNT, sm, st>>>(ctx->w1, ctx->w2, g, ctx->nhat, ctx->tw_y, ctx->tw_yh, ctx->tw_z);
+  yzh_kernel<E, S, P><<<g.Hx, kPlaneNT, sm, st>>>(ctx->w1, ctx->w2, g, ctx->nhat, ctx->tw_y, ctx->tw_yh, ctx->tw_z,
+                                                   ctx->flag);
   return launch_check("yzh_kernel");
 }
 
@@ -435,14 +505,16 @@ mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
   return MX_OK;
 }
 
-// kx-major octant [kx][comp][qz][qy] <-> [comp][qz][qy][kx]
+// plane-path octant (plane_octant_index) -> [comp][qz][qy][kx]
 __global__ void octant_to_cmajor_kernel(const float* __restrict__ src, float* __restrict__ dst, Grid g) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long no = (long)g.Hx * g.Oy * g.Oz;
   if (idx >= 6 * no) return;
   const int kx = (int)(idx % g.Hx);
-  const long rest = idx / g.Hx;  // (comp, qz, qy)
-  dst[idx] = src[(long)kx * 6 * g.Oz * g.Oy + rest];
+  const int qy = (int)((idx / g.Hx) % g.Oy);
+  const int qz = (int)((idx / ((long)g.Hx * g.Oy)) % g.Oz);
+  const int comp = (int)(idx / no);
+  dst[idx] = src[plane_octant_index(g, kx, comp, qz, qy)];
 }
 
 mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st) {

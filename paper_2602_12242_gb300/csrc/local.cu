@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoe
       }
     }
   }
-  if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, 1);
+  if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, kFlagNonfinite);
   io.out[idx] = make_float4(out.x, out.y, out.z, wout);
 }
 
@@ -74,7 +74,7 @@ __global__ void normalize_kernel(float4* m, long n, int* flag) {
   const float4 v = m[idx];
   const float r = rnorm3df(v.x, v.y, v.z);
   const float4 o = make_float4(v.x * r, v.y * r, v.z * r, 0.f);
-  if (!(isfinite(o.x) && isfinite(o.y) && isfinite(o.z))) atomicOr(flag, 1);
+  if (!(isfinite(o.x) && isfinite(o.y) && isfinite(o.z))) atomicOr(flag, kFlagNonfinite);
   m[idx] = o;
 }
 

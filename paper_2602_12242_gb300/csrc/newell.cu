@@ -292,7 +292,7 @@ __global__ void extract_octant_kernel(const double2* buf, int comp, Grid g, floa
   const int kz = (int)(idx / ((long)g.Hx * g.Oy));
   const double2 v = buf[((long)kz * g.Py + ky) * g.Px + kx];
   const double scale = -1.0 / ((double)g.Px * g.Py * g.Pz);
-  const long dst = kxmajor ? (((long)kx * 6 + comp) * g.Oz + kz) * g.Oy + ky : (long)comp * no + idx;
+  const long dst = kxmajor ? plane_octant_index(g, kx, comp, kz, ky) : (long)comp * no + idx;
   nhat[dst] = (float)(v.x * scale);
   // warp maxima first, then one atomic per warp
   unsigned long long re = (unsigned long long)__double_as_longlong(fabs(v.x));

@@ -78,8 +78,6 @@ template <int E, int S> struct LineFft {
   static constexpr int kPitch = (S > 1) ? E * (S + 1) : E;
 };
 
-// In-place FFT of `line` (natural order in and out).  `s` in [0, S); the S
-// threads of a line are consecutive lanes of one warp.  twL[q] = W_L^q.
 // Second step of line_fft: the twiddled E x S matrix is in rows k1 * (S + 1);
 // thread s does S-point FFTs over s for k1 = s + S j and writes X[k1 + E k2]
 // in natural order.
@@ -104,7 +102,12 @@ __device__ __forceinline__ void line_fft_step2(float2* line, int s) {
   __syncwarp();
 }
 
-template <int E, int S, bool INV, bool TW_SHARED = false>
+// In-place FFT of `line` (natural order in and out).  `s` in [0, S); the S
+// threads of a line are consecutive lanes of one warp.
+// TW_KS: twL is the product table twL[k * S + s] = W_L^(s k) (k < E, s < S),
+// which the S threads of a line read at consecutive addresses (no shared
+// memory bank conflicts, coalesced global loads); otherwise twL[q] = W_L^q.
+template <int E, int S, bool INV, bool TW_SHARED = false, bool TW_KS = false>
 __device__ __forceinline__ void line_fft(float2* line, int s, const float2* __restrict__ twL) {
   static_assert(E >= S && (E % S) == 0 && S <= 32, "line_fft shape");
   float2 v[E];
@@ -118,7 +121,8 @@ __device__ __forceinline__ void line_fft(float2* line, int s, const float2* __re
   }
 #pragma unroll
   for (int k = 1; k < E; ++k) {
-    float2 w = TW_SHARED ? twL[s * k] : __ldg(&twL[s * k]);
+    const int ti = TW_KS ? k * S + s : s * k;
+    float2 w = TW_SHARED ? twL[ti] : __ldg(&twL[ti]);
     if (INV) w.y = -w.y;
     v[k] = cmul(v[k], w);
   }
