@@ -161,20 +161,42 @@ __global__ void __launch_bounds__(3 * kRows * S, 2) xik_kernel(const float2* __r
 
 // ---------------------------------------------------------------------------
 // Per-kx plane: y FFT halves, z FFT + multiply + inverse z, inverse y.
+//
+// A cluster of two CTAs takes one kx plane: CTA h (its rank in the cluster)
+// computes the ky = 2 kyh + h half of the y spectrum (h = 1 multiplies the
+// input by W_Py^y first), the z stage of those columns and the inverse
+// Py/2-point y FFT.  The output is the sum of both halves (the odd half with
+// the conjugate twiddle), formed through distributed shared memory: CTA h
+// finishes lines [h L0, ...) of the plane with the other CTA's rows.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// generic address of the same shared-memory location in CTA `rank` of the cluster
+template <typename T> __device__ __forceinline__ const T* cluster_map(const T* p, unsigned rank) {
+  uint64_t out;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
+  return reinterpret_cast<const T*>(out);
+}
+
 template <int E, int S, int P>
-__global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restrict__ w1, float2* __restrict__ w2,
-                                                          Grid g, const float* __restrict__ nhk,
-                                                          const float2* __restrict__ twPy,
-                                                          const float2* __restrict__ twH,
-                                                          const float2* __restrict__ twz, int* flag) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
+    yzh_kernel(const float2* __restrict__ w1, float2* __restrict__ w2, Grid g, const float* __restrict__ nhk,
+               const float2* __restrict__ twPy, const float2* __restrict__ twH, const float2* __restrict__ twz,
+               int* flag) {
   constexpr int LH = E * S;                       // Py / 2
   constexpr int PITCH = YzhPitch<E, S>::value;
   constexpr int Q = P / 4;                        // points per residue class of kz
   constexpr int NT = kPlaneNT;
   extern __shared__ __align__(16) float2 sm[];
-  __shared__ __align__(8) uint64_t bar;           // completion of the bulk plane loads
-  const int kx = blockIdx.x;
+  __shared__ __align__(8) uint64_t bar;           // completion of the bulk plane load
+  const int h = (int)cluster_rank();
+  const int kx = blockIdx.x >> 1;
   const int tid = threadIdx.x;
   const int nz = g.nz, ny = g.ny;
   const int nlines = 3 * nz;
@@ -196,35 +218,29 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
   // 16-byte aligned too.  Odd ny takes the per-element path.
   const bool bulk = (ny & 1) == 0;
   const uint32_t row_bytes = (uint32_t)ny * sizeof(float2);
-  uint32_t parity = 0;
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
 
-  for (int h = 0; h < 2; ++h) {
-    constexpr int kB = 4;
-    if (bulk) {
-      fence_proxy_async_smem();
-      __syncthreads();  // the previous phase's shared-memory accesses are done
-      if (tid == 0) {
-        bulk_wait_read_all();  // the h = 0 bulk stores have read their rows
-        mbar_arrive_expect_tx(&bar, (uint32_t)nlines * row_bytes);
-        for (int line = 0; line < nlines; ++line)
-          bulk_load(sm + line * PITCH, w1 + kxoff + (long)line * ny, row_bytes, &bar);
+  if (bulk) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&bar, (uint32_t)nlines * row_bytes);
+      for (int line = 0; line < nlines; ++line)
+        bulk_load(sm + line * PITCH, w1 + kxoff + (long)line * ny, row_bytes, &bar);
+    }
+    for (int e = tid; e < nlines * (LH - ny); e += NT) {
+      const int line = e / (LH - ny), y = ny + e % (LH - ny);
+      sm[line * PITCH + y] = make_float2(0.f, 0.f);
+    }
+    if (!mbar_wait(&bar, 0)) atomicOr(flag, kFlagTimeout);
+    if (h) {
+      for (int e = tid; e < nlines * ny; e += NT) {
+        const int line = e / ny, y = e % ny;
+        sm[line * PITCH + y] = cmul(sm[line * PITCH + y], twS2[y]);
       }
-      for (int e = tid; e < nlines * (LH - ny); e += NT) {
-        const int line = e / (LH - ny), y = ny + e % (LH - ny);
-        sm[line * PITCH + y] = make_float2(0.f, 0.f);
-      }
-      if (!mbar_wait(&bar, parity)) atomicOr(flag, kFlagTimeout);
-      parity ^= 1;
-      if (h) {
-        for (int e = tid; e < nlines * ny; e += NT) {
-          const int line = e / ny, y = e % ny;
-          sm[line * PITCH + y] = cmul(sm[line * PITCH + y], twS2[y]);
-        }
-      }
-    } else
+    }
+  } else {
     // batches of kB independent loads per thread keep many requests in flight
+    constexpr int kB = 4;
     for (int e0 = tid; e0 < nlines * LH; e0 += NT * kB) {
       float2 v[kB];
 #pragma unroll
@@ -242,143 +258,148 @@ __global__ void __launch_bounds__(kPlaneNT, 1) yzh_kernel(const float2* __restri
         sm[line * PITCH + y] = (h && y < ny) ? cmul(v[u], twS2[y]) : v[u];
       }
     }
-    __syncthreads();
-    for (int l0 = 0; l0 < nlines; l0 += NT / S) {
-      const int l = l0 + tid / S;
-      line_fft<E, S, false, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
+  }
+  __syncthreads();
+  for (int l0 = 0; l0 < nlines; l0 += NT / S) {
+    const int l = l0 + tid / S;
+    line_fft<E, S, false, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
+  }
+  __syncthreads();
+  // z stage: 4 lanes per ky column, lane r owns kz = 4q + r
+  for (int task = tid; task < 4 * LH; task += NT) {
+    const int kyh = task >> 2, r = task & 3;
+    const float2* wz = twZ + r * 2 * Q;
+    const int ky = 2 * kyh + h;
+    const bool fy = ky > (g.Py >> 1);
+    const int qy = fy ? g.Py - ky : ky;
+    // tensor values of this lane's kz = 4q + r, loaded first so that they
+    // arrive while the forward z FFTs run
+    float tn[Q][6];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int kz = 4 * q + r;
+      const bool fz = kz > (P >> 1);
+      const int qz = fz ? P - kz : kz;
+      // the six components of (qz, qy) are contiguous (8-byte aligned)
+      const float2* t = reinterpret_cast<const float2*>(nk + (((long)qz * 2 + h) * oyh + (qy >> 1)) * 6);
+      const float2 t01 = __ldg(t), t23 = __ldg(t + 1), t45 = __ldg(t + 2);
+      tn[q][0] = t01.x;
+      tn[q][1] = t01.y;
+      tn[q][2] = t23.x;
+      tn[q][3] = fy ? -t23.y : t23.y;
+      tn[q][4] = fz ? -t45.x : t45.x;
+      tn[q][5] = (fy != fz) ? -t45.y : t45.y;
     }
-    __syncthreads();
-    // z stage: 4 lanes per ky column, lane r owns kz = 4q + r
-    for (int task = tid; task < 4 * LH; task += NT) {
-      const int kyh = task >> 2, r = task & 3;
-      const float2* wz = twZ + r * 2 * Q;
-      const int ky = 2 * kyh + h;
-      const bool fy = ky > (g.Py >> 1);
-      const int qy = fy ? g.Py - ky : ky;
-      // tensor values of this lane's kz = 4q + r, loaded first so that they
-      // arrive while the forward z FFTs run
-      float tn[Q][6];
+    float2 Z[3][Q];
 #pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int kz = 4 * q + r;
-        const bool fz = kz > (P >> 1);
-        const int qz = fz ? P - kz : kz;
-        // the six components of (qz, qy) are contiguous (8-byte aligned)
-        const float2* t = reinterpret_cast<const float2*>(nk + (((long)qz * 2 + h) * oyh + (qy >> 1)) * 6);
-        const float2 t01 = __ldg(t), t23 = __ldg(t + 1), t45 = __ldg(t + 2);
-        tn[q][0] = t01.x;
-        tn[q][1] = t01.y;
-        tn[q][2] = t23.x;
-        tn[q][3] = fy ? -t23.y : t23.y;
-        tn[q][4] = fz ? -t45.x : t45.x;
-        tn[q][5] = (fy != fz) ? -t45.y : t45.y;
-      }
-      float2 Z[3][Q];
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int n = 0; n < Q; ++n) {
-          float2 a = make_float2(0.f, 0.f), b = a;
-          if (n < nz) a = sm[(c * nz + n) * PITCH + kyh];
-          if (n + Q < nz) b = sm[(c * nz + n + Q) * PITCH + kyh];
-          // y_r[n] = x[n] W_P^(r n) + x[n + Q] W_P^(r (n + Q))
-          Z[c][n] = cadd(cmul(a, wz[n]), cmul(b, wz[n + Q]));
-        }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) RegFft<Q, false>::run(Z[c]);
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const float nxx = tn[q][0], nyy = tn[q][1], nzz = tn[q][2];
-        const float nxy = tn[q][3], nxz = tn[q][4], nyz = tn[q][5];
-        const float2 mx = Z[0][q], my = Z[1][q], mz = Z[2][q];
-        Z[0][q] = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
-        Z[1][q] = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
-        Z[2][q] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+      for (int n = 0; n < Q; ++n) {
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (n < nz) a = sm[(c * nz + n) * PITCH + kyh];
+        if (n + Q < nz) b = sm[(c * nz + n + Q) * PITCH + kyh];
+        // y_r[n] = x[n] W_P^(r n) + x[n + Q] W_P^(r (n + Q))
+        Z[c][n] = cadd(cmul(a, wz[n]), cmul(b, wz[n + Q]));
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) RegFft<Q, true>::run(Z[c]);
-      // x[n] = sum_r W_P^(-r n) u_r[n mod Q] for n < 2Q, summed over the 4 lanes:
-      // xor 2 leaves each lane pair one half [hb, hb + Q), xor 1 one quarter
-      const int hb = (r >> 1) * Q;
+    for (int c = 0; c < 3; ++c) RegFft<Q, false>::run(Z[c]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float2 sacc[Q];
+    for (int q = 0; q < Q; ++q) {
+      const float nxx = tn[q][0], nyy = tn[q][1], nzz = tn[q][2];
+      const float nxy = tn[q][3], nxz = tn[q][4], nyz = tn[q][5];
+      const float2 mx = Z[0][q], my = Z[1][q], mz = Z[2][q];
+      Z[0][q] = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
+      Z[1][q] = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
+      Z[2][q] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
+    }
 #pragma unroll
-        for (int n = 0; n < Q; ++n) {
-          const float2 lo = cmul(Z[c][n], cconj(wz[n]));      // term n
-          const float2 hi = cmul(Z[c][n], cconj(wz[n + Q]));  // term n + Q
-          const float2 keep = (r >> 1) ? hi : lo;
-          const float2 give = (r >> 1) ? lo : hi;
+    for (int c = 0; c < 3; ++c) RegFft<Q, true>::run(Z[c]);
+    // x[n] = sum_r W_P^(-r n) u_r[n mod Q] for n < 2Q, summed over the 4 lanes:
+    // xor 2 leaves each lane pair one half [hb, hb + Q), xor 1 one quarter
+    const int hb = (r >> 1) * Q;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 sacc[Q];
+#pragma unroll
+      for (int n = 0; n < Q; ++n) {
+        const float2 lo = cmul(Z[c][n], cconj(wz[n]));      // term n
+        const float2 hi = cmul(Z[c][n], cconj(wz[n + Q]));  // term n + Q
+        const float2 keep = (r >> 1) ? hi : lo;
+        const float2 give = (r >> 1) ? lo : hi;
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, give.x, 2);
+        o.y = __shfl_xor_sync(0xffffffffu, give.y, 2);
+        sacc[n] = cadd(keep, o);
+      }
+      if constexpr (Q >= 2) {
+#pragma unroll
+        for (int n = 0; n < Q / 2; ++n) {
+          const float2 keep = (r & 1) ? sacc[n + Q / 2] : sacc[n];
+          const float2 give = (r & 1) ? sacc[n] : sacc[n + Q / 2];
           float2 o;
-          o.x = __shfl_xor_sync(0xffffffffu, give.x, 2);
-          o.y = __shfl_xor_sync(0xffffffffu, give.y, 2);
-          sacc[n] = cadd(keep, o);
-        }
-        if constexpr (Q >= 2) {
-#pragma unroll
-          for (int n = 0; n < Q / 2; ++n) {
-            const float2 keep = (r & 1) ? sacc[n + Q / 2] : sacc[n];
-            const float2 give = (r & 1) ? sacc[n] : sacc[n + Q / 2];
-            float2 o;
-            o.x = __shfl_xor_sync(0xffffffffu, give.x, 1);
-            o.y = __shfl_xor_sync(0xffffffffu, give.y, 1);
-            const int idx = hb + (r & 1) * (Q / 2) + n;
-            if (idx < nz) sm[(c * nz + idx) * PITCH + kyh] = cadd(keep, o);
-          }
-        } else {
-          float2 o;
-          o.x = __shfl_xor_sync(0xffffffffu, sacc[0].x, 1);
-          o.y = __shfl_xor_sync(0xffffffffu, sacc[0].y, 1);
-          if ((r & 1) == 0 && hb < nz) sm[(c * nz + hb) * PITCH + kyh] = cadd(sacc[0], o);
-        }
-      }
-    }
-    __syncthreads();
-    for (int l0 = 0; l0 < nlines; l0 += NT / S) {
-      const int l = l0 + tid / S;
-      line_fft<E, S, true, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
-    }
-    __syncthreads();
-    if (h == 0) {
-      if (bulk) {
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-          for (int line = 0; line < nlines; ++line)
-            bulk_store(w2 + kxoff + (long)line * ny, sm + line * PITCH, row_bytes);
-          bulk_commit();
+          o.x = __shfl_xor_sync(0xffffffffu, give.x, 1);
+          o.y = __shfl_xor_sync(0xffffffffu, give.y, 1);
+          const int idx = hb + (r & 1) * (Q / 2) + n;
+          if (idx < nz) sm[(c * nz + idx) * PITCH + kyh] = cadd(keep, o);
         }
       } else {
-        for (int e = tid; e < nlines * ny; e += NT) {
-          const int line = e / ny, y = e % ny;
-          w2[kxoff + (long)line * ny + y] = sm[line * PITCH + y];
-        }
-      }
-    } else {
-      if (bulk && tid == 0) bulk_wait_all();  // the h = 0 rows are in w2
-      __syncthreads();
-      for (int e0 = tid; e0 < nlines * ny; e0 += NT * kB) {
-        float2 prev[kB];
-#pragma unroll
-        for (int u = 0; u < kB; ++u) {
-          const int e = e0 + u * NT;
-          if (e < nlines * ny) {
-            const int line = e / ny, y = e % ny;
-            prev[u] = w2[kxoff + (long)line * ny + y];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kB; ++u) {
-          const int e = e0 + u * NT;
-          if (e >= nlines * ny) break;
-          const int line = e / ny, y = e % ny;
-          const float2 v = cmul(sm[line * PITCH + y], cconj(twS2[y]));
-          w2[kxoff + (long)line * ny + y] = cadd(prev[u], v);
-        }
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, sacc[0].x, 1);
+        o.y = __shfl_xor_sync(0xffffffffu, sacc[0].y, 1);
+        if ((r & 1) == 0 && hb < nz) sm[(c * nz + hb) * PITCH + kyh] = cadd(sacc[0], o);
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
+  for (int l0 = 0; l0 < nlines; l0 += NT / S) {
+    const int l = l0 + tid / S;
+    line_fft<E, S, true, true, true>(l < nlines ? sm + l * PITCH : dummy, tid % S, twS);
+  }
+  // both halves' inverse-y rows are in shared memory
+  cluster_sync_all();
+  const float2* other = cluster_map(sm, (unsigned)(h ^ 1));
+  const int L0 = (nlines + 1) >> 1;
+  const int lb = h ? L0 : 0, le = h ? nlines : L0;
+  {
+    constexpr int kB = 4;  // independent remote loads in flight per thread
+    const int cnt = (le - lb) * ny;
+    for (int e0 = tid; e0 < cnt; e0 += NT * kB) {
+      float2 rv[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int e = e0 + u * NT;
+        if (e < cnt) rv[u] = other[(lb + e / ny) * PITCH + e % ny];
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int e = e0 + u * NT;
+        if (e >= cnt) break;
+        const int line = lb + e / ny, y = e % ny;
+        const float2 tw = cconj(twS2[y]);
+        const float2 own = sm[line * PITCH + y];
+        // even half + W_Py^(-y) x odd half
+        sm[line * PITCH + y] = h ? cadd(cmul(own, tw), rv[u]) : cadd(own, cmul(rv[u], tw));
+      }
+    }
+  }
+  if (bulk) {
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      for (int line = lb; line < le; ++line) bulk_store(w2 + kxoff + (long)line * ny, sm + line * PITCH, row_bytes);
+      bulk_commit();
+    }
+  } else {
+    __syncthreads();
+    for (int e = tid; e < (le - lb) * ny; e += NT) {
+      const int line = lb + e / ny, y = e % ny;
+      w2[kxoff + (long)line * ny + y] = sm[line * PITCH + y];
+    }
+  }
+  // the other CTA has finished reading this CTA's rows; this CTA's bulk
+  // stores have read them before it exits
+  cluster_sync_all();
+  if (bulk && tid == 0) bulk_wait_read_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -426,7 +447,7 @@ static mx_status yzh_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(yzh_kernel<E, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
-  yzh_kernel<E, S, P><<<g.Hx, kPlaneNT, sm, st>>>(ctx->w1, ctx->w2, g, ctx->nhat, ctx->tw_y, ctx->tw_yh, ctx->tw_z,
+  yzh_kernel<E, S, P><<<2 * g.Hx, kPlaneNT, sm, st>>>(ctx->w1, ctx->w2, g, ctx->nhat, ctx->tw_y, ctx->tw_yh, ctx->tw_z,
                                                    ctx->flag);
   return launch_check("yzh_kernel");
 }
