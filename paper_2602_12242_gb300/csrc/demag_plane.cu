@@ -46,7 +46,7 @@ template <int E, int S> struct YzhPitch {
 // x forward into the kx-major spectrum.
 // ---------------------------------------------------------------------------
 template <int E, int S>
-__global__ void __launch_bounds__(3 * kRows * S, 2) xfk_kernel(const float4* __restrict__ m, Grid g, float ms,
+__global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xfk_kernel(const float4* __restrict__ m, Grid g, float ms,
                                                             const float* __restrict__ ms_map, float2* __restrict__ w1,
                                                             const float2* __restrict__ twM,
                                                             const float2* __restrict__ twP) {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(3 * kRows * S, 2) xfk_kernel(const float4* __r
 // x inverse from the kx-major spectrum.
 // ---------------------------------------------------------------------------
 template <int E, int S>
-__global__ void __launch_bounds__(3 * kRows * S, 2) xik_kernel(const float2* __restrict__ w2, Grid g,
+__global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(const float2* __restrict__ w2, Grid g,
                                                             float4* __restrict__ hd, const float2* __restrict__ twM,
                                                             const float2* __restrict__ twP) {
   constexpr int M = E * S;
@@ -205,13 +205,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
   float2* twS = dummy + PITCH;                    // W_LH^(s k) at [k S + s], in shared memory
   const int oyh = (g.Oy + 1) >> 1;
   const float* nk = nhk + plane_octant_index(g, kx, 0, 0, 0);
-  float2* twZ = twS + LH;                         // W_P^(r n) for r < 4, n < 2Q
-  float2* twS2 = twZ + 64;                        // W_Py^y, y < Py/2
+  float2* twZ = twS + LH;                         // W_P^(r n) at [r (2Q + 1) + n], r < 4, n < 2Q
+  float2* twS2 = twZ + 68;                        // W_Py^y, y < Py/2
   for (int q = tid; q < LH; q += NT) {
     twS[q] = __ldg(&twH[(q % S) * (q / S)]);  // (S - 1)(E - 1) < LH
     twS2[q] = __ldg(&twPy[q]);
   }
-  for (int q = tid; q < 8 * Q; q += NT) twZ[q] = __ldg(&twz[((q / (2 * Q)) * (q % (2 * Q))) % P]);
+  // rows of 2Q + 1 entries: the four lanes of a column read four banks
+  for (int q = tid; q < 8 * Q; q += NT) twZ[(q / (2 * Q)) * (2 * Q + 1) + q % (2 * Q)] = __ldg(&twz[((q / (2 * Q)) * (q % (2 * Q))) % P]);
   // Rows of w1/w2 are ny float2 at 8 ny-byte strides: with ny even every row
   // starts on a 16-byte boundary and has a 16-byte multiple size, so the plane
   // moves by bulk copies (one per row); the line pitch keeps the shared rows
@@ -268,7 +269,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
   // z stage: 4 lanes per ky column, lane r owns kz = 4q + r
   for (int task = tid; task < 4 * LH; task += NT) {
     const int kyh = task >> 2, r = task & 3;
-    const float2* wz = twZ + r * 2 * Q;
+    const float2* wz = twZ + r * (2 * Q + 1);
     const int ky = 2 * kyh + h;
     const bool fy = ky > (g.Py >> 1);
     const int qy = fy ? g.Py - ky : ky;
@@ -407,7 +408,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
 // ---------------------------------------------------------------------------
 template <int E, int S> static size_t xk_smem() { return sizeof(float2) * 3 * kRows * (LineFft<E, S>::kPitch + 1); }
 template <int E, int S> static size_t yzh_smem(int nz) {
-  return sizeof(float2) * ((3 * nz + 1) * YzhPitch<E, S>::value + 2 * E * S + 64);
+  return sizeof(float2) * ((3 * nz + 1) * YzhPitch<E, S>::value + 2 * E * S + 68);
 }
 
 template <int E, int S>
