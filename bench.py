@@ -147,8 +147,11 @@ def workload(name):
     return cfg, m0, Ms, Ku, axis
 
 
-def algorithmic_bytes(cfg, P):
-    """Algorithmic HBM bytes per launch of each kernel (FP32 spectra, float4 fields)."""
+def algorithmic_bytes(cfg, P, ms_map=False, anis_map=False):
+    """Algorithmic HBM bytes per launch of each kernel (FP32 spectra, float4
+    fields; a per-cell Ms map adds 4 B/cell to the x pass and the local
+    kernel, an anisotropy map (Ku float + axis float4) 20 B/cell to the local
+    kernel)."""
     nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
     Px, Py, Pz = P
     Hx = Px // 2 + 1 if Px > 1 else 1
@@ -156,15 +159,16 @@ def algorithmic_bytes(cfg, P):
     w1 = 3 * nz * ny * Hx * 8           # spectrum after the x pass
     w2 = 3 * nz * Py * Hx * 8           # after the y pass
     tensor = (6 if Pz > 1 else 4) * (Pz // 2 + 1) * (Py // 2 + 1) * Hx * 4
+    maps = (4 if ms_map else 0) + (20 if anis_map else 0)
     return {
-        "x_fwd": nc * 16 + w1,
+        "x_fwd": nc * (16 + (4 if ms_map else 0)) + w1,
         "y_fwd": w1 + w2,
         "z_mul": 2 * w2 + tensor,
         "y_inv": w2 + w1,
         "yz_fused": 2 * w1 + tensor,
         "x_inv": w1 + nc * 16,
-        # RK4 stage average: (64 + 96 + 96 + 80) / 4 bytes per cell
-        "local_stage": nc * 84,
+        # RK4 stage average: (64 + 96 + 96 + 80) / 4 bytes per cell, plus the maps
+        "local_stage": nc * (84 + maps),
         "normalize": nc * 32,
         "copy": nc * 32,
     }
@@ -246,7 +250,8 @@ def run_mx(args, rank, world, local, name, with_extras=True):
     prof = ctx.profile_step(m, K, dt)
     ctx.sync()
     P = ctx.padded_dims
-    ab = algorithmic_bytes(cfg, P)
+    ab = algorithmic_bytes(cfg, P, ms_map=not np.isscalar(Ms),
+                           anis_map=not (np.isscalar(Ku) and np.asarray(axis).ndim <= 1))
     launches = sum(c for (_, c) in prof.values())
     per_step = (launches - 1) / K  # one normalisation per call
     res["launches_per_step"] = per_step
@@ -389,7 +394,8 @@ def main():
         return
     line = {
         "metric": "cell-steps/s (full H_eff+LLG RK4 step)",
-        "value": res["value"], "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
+        "value": res["value"], "unit": "cell-steps/s", "cell_stages_per_s": 4 * res["value"],
+        "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
         "config": {"workload": WORKLOADS[name], "cells": c["nx"] * c["ny"] * c["nz"],
