@@ -15,6 +15,11 @@ adjoint: time of the recorded forward plus the reverse sweep against the
 
 trajectory: snapshots of m every --every RK4 steps of a workload from its
   seeded initial state (for the FP32-vs-FP64 divergence curve).
+
+  python -m paper_2602_12242_gb300.patterns --fft-mode-timing
+
+fft-mode timing: per-kernel time of the bulk RK4 step with FP32 x transforms
+  and with the split-BF16 DFT-as-GEMM first x stage.
 """
 import argparse
 import json
@@ -118,6 +123,22 @@ def adjoint_report(nsteps=2000, every=100):
             "grad_m0_norm": float(g[..., :3].norm()), "grad_ms_norm": float(gms.norm())}
 
 
+def fft_mode_timing(name="bulk", steps=20):
+    """Per-kernel microseconds per launch of one workload's RK4 step with the
+    FP32 x transforms and with the split-BF16 DFT-as-GEMM first x stage."""
+    cfg = dict(inputs.CONFIGS[name])
+    Ms, Ku, axis = inputs.material(name)
+    out = {}
+    for label, mode in (("fp32", L.MX_FFT_FP32), ("split_bf16", L.MX_FFT_SPLIT_BF16)):
+        ctx = Context.from_config(cfg, Ms=Ms, Ku=Ku, ku_axis=axis, fft_mode=mode)
+        m = to_dev4(inputs.initial_m(name))
+        prof = ctx.profile_step(m, steps, cfg["dt"])
+        ctx.sync()
+        out[label] = {k: round(1e3 * v[0] / v[1], 2) for k, v in prof.items()}
+        ctx.close()
+    return out
+
+
 def trajectory(name, steps, every):
     """m (float32, (n_snap, nz, ny, nx, 3)) at steps 0, every, 2 every, ... of
     a workload's RK4 run from its seeded initial state, and those step counts."""
@@ -144,6 +165,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--npz", default=None)
+    ap.add_argument("--fft-mode-timing", action="store_true")
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--batch", type=int, default=128)
@@ -152,6 +174,9 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    if a.fft_mode_timing:
+        print(json.dumps(fft_mode_timing()), flush=True)
+        return
     if a.trajectory:
         snaps, at = trajectory(a.trajectory, a.steps, a.every)
         np.savez_compressed(a.npz or f"{a.trajectory}_fp32.npz", m=snaps, step=at)

@@ -64,6 +64,41 @@ def test_split_bf16_dft_stage_error():
     assert ei.value.status == _lib.MX_ERR_UNSUPPORTED
 
 
+def test_split_bf16_bulk_energy_and_trajectory():
+    """Split-BF16 stage on the full bulk grid: the five energies at t = 0
+    against the FP64 oracle (bound 1e-4 of the sum of the terms, the mode's
+    bound), and m after 200 RK4 steps against the FP32 path, next to the FP32
+    path's own response to a 2^-24 relative perturbation of m0."""
+    from paper_2602_12242_gb300 import _lib, inputs
+    from paper_2602_12242_gb300.solver import from_dev4, to_dev4
+    c = dict(inputs.CONFIGS["bulk"])
+    m0 = f32(inputs.initial_m("bulk"))
+    _, _, axis = inputs.material("bulk")
+    axis = f32(axis)
+    ctx_s = context(c, axis=axis, fft_mode=_lib.MX_FFT_SPLIT_BF16)
+    e_s = ctx_s.energy(to_dev4(m0))
+    e_r = mm.energies(problem(c, axis=axis), t64(m0))
+    scale = sum(abs(v) for v in e_r.values())
+    de = max(abs(e_s[k] - e_r[k]) for k in e_r) / scale
+    nsteps = 200
+    ms = to_dev4(m0)
+    ctx_s.rk_step(ms, nsteps, c["dt"])
+    ctx_s.sync()
+    ctx_f = context(c, axis=axis)
+    mf = to_dev4(m0)
+    ctx_f.rk_step(mf, nsteps, c["dt"])
+    pert = m0 * (1.0 + 2.0 ** -24 * np.random.default_rng(62).choice([-1.0, 1.0], size=m0.shape))
+    mp = to_dev4(pert)
+    ctx_f.rk_step(mp, nsteps, c["dt"])
+    ctx_f.sync()
+    d = float(np.abs(from_dev4(ms) - from_dev4(mf)).max())
+    sens = float(np.abs(from_dev4(mp) - from_dev4(mf)).max())
+    print(f"\nsplit-BF16 bulk: energy max term error / sum of terms at t=0 {de:.2e}; "
+          f"m after {nsteps} steps vs FP32 path max {d:.2e} (FP32 self-sensitivity {sens:.2e})")
+    assert de <= 1e-4
+    assert d <= max(1e-3, 5.0 * sens)
+
+
 def test_bulk_crop_trajectory_and_energy_precision():
     from paper_2602_12242_gb300 import inputs
     from paper_2602_12242_gb300.solver import from_dev4, to_dev4
