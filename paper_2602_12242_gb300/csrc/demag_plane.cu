@@ -315,22 +315,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) RegFft<Q, true>::run(Z[c]);
-    // x[n] = sum_r W_P^(-r n) u_r[n mod Q] for n < 2Q, summed over the 4 lanes:
-    // xor 2 leaves each lane pair one half [hb, hb + Q), xor 1 one quarter
+    // x[n] = sum_r W_P^(-r n) u_r[n mod Q] for n < 2Q, summed over the 4 lanes.
+    // With t_r[m] = W_P^(-r m) u_r[m] (m < Q) and W_P^(-r Q) = i^r:
+    //   x[m] = t0 + t1 + t2 + t3,  x[m + Q] = (t0 - t2) + i (t1 - t3).
+    // Round 1 (xor 2): lanes 0, 1 form t_r + t_(r+2); lanes 2, 3 form
+    // t_(r-2) - t_r (lane 3 then times i).  Round 2 (xor 1) sums the pairs
+    // and leaves each lane a quarter of the outputs.
     const int hb = (r >> 1) * Q;
+    const float sgn = (r >> 1) ? -1.f : 1.f;
+    const bool times_i = r == 3;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float2 sacc[Q];
 #pragma unroll
       for (int n = 0; n < Q; ++n) {
-        const float2 lo = cmul(Z[c][n], cconj(wz[n]));      // term n
-        const float2 hi = cmul(Z[c][n], cconj(wz[n + Q]));  // term n + Q
-        const float2 keep = (r >> 1) ? hi : lo;
-        const float2 give = (r >> 1) ? lo : hi;
+        const float2 t = cmul(Z[c][n], cconj(wz[n]));
         float2 o;
-        o.x = __shfl_xor_sync(0xffffffffu, give.x, 2);
-        o.y = __shfl_xor_sync(0xffffffffu, give.y, 2);
-        sacc[n] = cadd(keep, o);
+        o.x = __shfl_xor_sync(0xffffffffu, t.x, 2);
+        o.y = __shfl_xor_sync(0xffffffffu, t.y, 2);
+        const float2 v = make_float2(fmaf(sgn, t.x, o.x), fmaf(sgn, t.y, o.y));
+        sacc[n] = times_i ? make_float2(-v.y, v.x) : v;
       }
       if constexpr (Q >= 2) {
 #pragma unroll
