@@ -361,6 +361,20 @@ def run(p, m, dt, nsteps, method="rk4"):
 # Energies (J)
 # --------------------------------------------------------------------------
 
+def exchange_energy_central(p, m):
+    """Exchange energy V sum_cells A |grad m|^2 with every derivative a
+    second-order central difference (m_{i+1} - m_{i-1}) / (2h) over the same
+    ghost cells as the field (Eq. for e_exch in Sec. II-A with the central
+    stencils of Sec. II-B).  This is the energy the paper tabulates; the
+    exchange term of ``energies`` is the variational one (-mu0/2 Ms m.H_exch,
+    face differences), whose gradient is the field."""
+    mp = ghosted(p, m)
+    gx = (mp[1:-1, 1:-1, 2:] - mp[1:-1, 1:-1, :-2]) / (2 * p.dx)
+    gy = (mp[1:-1, 2:, 1:-1] - mp[1:-1, :-2, 1:-1]) / (2 * p.dy)
+    gz = (mp[2:, 1:-1, 1:-1] - mp[:-2, 1:-1, 1:-1]) / (2 * p.dz)
+    return float(p.V * p.A * ((gx ** 2).sum() + (gy ** 2).sum() + (gz ** 2).sum()))
+
+
 def energies(p, m):
     """Demag, exchange, DMI: -mu0/2 V sum Ms m.H_term; anisotropy: V sum Ku[1-(e.m)^2];
     Zeeman: -mu0 V sum Ms m.H_bias (Sec. II-A energy densities, with the Ms factor
