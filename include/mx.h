@@ -178,6 +178,19 @@ mx_status mx_rk_step(mx_ctx *ctx, float *m, int nsteps, double dt, int method,
  * FP64.  e_out is a HOST array.  Synchronises `stream`. */
 mx_status mx_energy(mx_ctx *ctx, const float *m, double e_out[5], mx_stream_t stream);
 
+/* Exchange energy [J] of m as the paper tabulates it (Sec. III-B, Table I):
+ * V sum_cells A |grad m|^2 (the e_exch density of Sec. II-A) with every
+ * derivative the second-order central difference (m_+ - m_-)/(2h) of
+ * Sec. II-B, over the same ghost cells as the exchange field (Neumann, or the
+ * chiral ghosts with DMI).  mx_energy's exchange term is the variational form
+ * -mu0/2 Ms m.H_exch (face differences), whose gradient is the field; the two
+ * differ at O(h^2).
+ *   m      DEVICE float4 field, nx*ny*nz records (read only)
+ *   e_out  HOST pointer to one double
+ * Synchronises `stream`.  Errors: MX_ERR_INVALID_ARG for a NULL or misaligned
+ * pointer. */
+mx_status mx_exchange_energy_central(mx_ctx *ctx, const float *m, double *e_out, mx_stream_t stream);
+
 /* Energies [J] like mx_energy, for callers that cannot allocate device
  * memory -- code that runs inside a device-memory budget owned by another
  * framework, or a latency-critical loop where an allocation's implicit

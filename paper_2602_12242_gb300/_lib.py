@@ -57,6 +57,7 @@ SIGNATURES = {
     "mx_llg_rhs": (_I, [_P, _P, _P, _P]),
     "mx_rk_step": (_I, [_P, _P, _I, _D, _I, _P]),
     "mx_energy": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
+    "mx_exchange_energy_central": (_I, [_P, _P, ctypes.POINTER(_D), _P]),
     "mx_sync": (_I, [_P, _P]),
     "mx_padded_dims": (_I, [_P, ctypes.POINTER(_I)]),
     "mx_demag_tensor_real": (_I, [_P, _P, _P]),
@@ -163,6 +164,12 @@ def mx_energy(ctx, m, stream=None):
     out = (_D * 5)()
     check(lib().mx_energy(ctx, ptr(m), out, stream_handle(stream)))
     return list(out)
+
+
+def mx_exchange_energy_central(ctx, m, stream=None):
+    out = _D()
+    check(lib().mx_exchange_energy_central(ctx, ptr(m), ctypes.byref(out), stream_handle(stream)))
+    return out.value
 
 
 def mx_sync(ctx, stream=None):

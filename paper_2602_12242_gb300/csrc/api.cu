@@ -495,6 +495,21 @@ mx_status mx_energy(mx_ctx* ctx, const float* m, double e_out[5], mx_stream_t st
   return MX_OK;
 }
 
+mx_status mx_exchange_energy_central(mx_ctx* ctx, const float* m, double* e_out, mx_stream_t stream) {
+  MX_TRY(check_ctx(ctx));
+  MX_TRY(check_vec_ptr(m, "mx_exchange_energy_central: m"));
+  if (!e_out) {
+    set_error("mx_exchange_energy_central: NULL e_out");
+    return MX_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  MX_CUDA_TRY(cudaMemsetAsync(ctx->ered, 0, sizeof(double), st));
+  MX_TRY(exchange_energy_central(ctx, (const float4*)m, ctx->ered, st));
+  MX_CUDA_TRY(cudaMemcpyAsync(e_out, ctx->ered, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MX_CUDA_TRY(cudaStreamSynchronize(st));
+  return MX_OK;
+}
+
 mx_status mx_sync(mx_ctx* ctx, mx_stream_t stream) {
   MX_TRY(check_ctx(ctx));
   cudaStream_t st = (cudaStream_t)stream;

@@ -80,5 +80,6 @@ mx_status local_stage(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st)
 mx_status normalize_field(mx_ctx* ctx, float4* m, cudaStream_t st);
 mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t st);
 mx_status energy_terms(mx_ctx* ctx, const float4* m, const float4* hd, double* e_dev, cudaStream_t st);
+mx_status exchange_energy_central(mx_ctx* ctx, const float4* m, double* e_dev, cudaStream_t st);
 
 }  // namespace mx

@@ -29,43 +29,7 @@ __global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoe
   const int k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
   const long idx = ((long)k * g.ny + j) * g.nx + i;
-  const float3 mc = f3(io.m[idx]);
-  const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
-  const float inv_ms = 1.f / ms;
-  Terms t;
-  local_terms<DMI>(io.m, io.hd, g, c, i, j, k, idx, mc, inv_ms, t);
-  float3 out;
-  float wout = 0.f;  // |u| of a renormalised stage output (used by the adjoint)
-  if (MODE == LM_HEFF) {
-    out = make_float3(0.f, 0.f, 0.f);
-    if (io.terms & MX_TERM_DEMAG) out = out + t.demag;
-    if (io.terms & MX_TERM_EXCH) out = out + t.exch;
-    if (io.terms & MX_TERM_ANIS) out = out + t.anis;
-    if (io.terms & MX_TERM_DMI) out = out + t.dmi;
-    if (io.terms & MX_TERM_ZEEMAN) out = out + t.zee;
-  } else {
-    const float3 H = t.demag + t.exch + t.anis + t.dmi + t.zee;
-    const float3 kk = llg(c, mc, H);
-    if (MODE == LM_RHS) {
-      out = kk;
-    } else if (MODE == LM_EULER) {
-      out = unit_norm(mc + io.dt * kk, wout);
-    } else if (MODE == LM_RK4_S0) {
-      io.acc[idx] = make_float4(kk.x, kk.y, kk.z, 0.f);
-      out = unit_norm(mc + (0.5f * io.dt) * kk, wout);
-    } else {
-      const float3 m0 = f3(io.m0[idx]);
-      const float3 a = f3(io.acc[idx]);
-      if (MODE == LM_RK4_S3) {
-        out = unit_norm(m0 + (io.dt * (1.f / 6.f)) * (a + kk), wout);
-      } else {
-        io.acc[idx] = make_float4(a.x + 2.f * kk.x, a.y + 2.f * kk.y, a.z + 2.f * kk.z, 0.f);
-        out = unit_norm(m0 + ((MODE == LM_RK4_S1 ? 0.5f : 1.f) * io.dt) * kk, wout);
-      }
-    }
-  }
-  if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, kFlagNonfinite);
-  io.out[idx] = make_float4(out.x, out.y, out.z, wout);
+  local_cell<MODE, DMI>(io, g, c, i, j, k, idx, flag);
 }
 
 __global__ void normalize_kernel(float4* m, long n, int* flag) {
@@ -204,6 +168,47 @@ mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t s
   ProfScope ps(ctx, KID_COPY, st);
   copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, src, n);
   return launch_check("copy_kernel");
+}
+
+// Exchange energy A V sum |grad m|^2 with second-order central differences
+// (m_+ - m_-)/(2h) over the field's ghost cells; FP64 block sums, one atomic
+// per block.
+__global__ void __launch_bounds__(256) exch_central_kernel(const float4* __restrict__ m, Grid g, LocalCoef c,
+                                                           double AV, double inv4dx2, double inv4dy2,
+                                                           double inv4dz2, double* e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double acc = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const long idx = ((long)k * g.ny + j) * g.nx + i;
+    const float3 mc = f3(m[idx]);
+    float3 xp, xm, yp, ym, zp, zm;
+    neighbours(m, g, c, i, j, k, idx, mc, xp, xm, yp, ym, zp, zm);
+    const float3 dx = xp - xm, dy = yp - ym, dz = zp - zm;
+    acc = AV * (inv4dx2 * (double)dot3(dx, dx) + inv4dy2 * (double)dot3(dy, dy) + inv4dz2 * (double)dot3(dz, dz));
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((t & 31) == 0) red[t >> 5] = acc;
+  __syncthreads();
+  if (t == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x * blockDim.y) / 32; ++w) sum += red[w];
+    atomicAdd(e, sum);
+  }
+}
+
+mx_status exchange_energy_central(mx_ctx* ctx, const float4* m, double* e_dev, cudaStream_t st) {
+  const Grid& g = ctx->g;
+  const LocalCoef c = local_coef(ctx);
+  dim3 grid, block;
+  local_dims(g, grid, block);
+  const mx_params& p = ctx->p;
+  exch_central_kernel<<<grid, block, 0, st>>>(m, g, c, p.A * p.dx * p.dy * p.dz, 0.25 / (p.dx * p.dx),
+                                              0.25 / (p.dy * p.dy), 0.25 / (p.dz * p.dz), e_dev);
+  return launch_check("exch_central_kernel");
 }
 
 mx_status energy_terms(mx_ctx* ctx, const float4* m, const float4* hd, double* e_dev, cudaStream_t st) {

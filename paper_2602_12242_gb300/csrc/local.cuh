@@ -5,6 +5,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "kernels.cuh"
 
 namespace mx {
 
@@ -21,20 +22,29 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-// All field terms at cell (i, j, k).
-template <bool DMI>
-__device__ __forceinline__ void local_terms(const float4* __restrict__ m, const float4* __restrict__ hd,
-                                            const Grid& g, const LocalCoef& c, int i, int j, int k, long idx,
-                                            float3 mc, float inv_ms, Terms& t) {
+// The six face neighbours of cell (i, j, k), with the ghost cells of the
+// boundary condition where a neighbour is missing: the chiral ghost
+// m_b - h (D/2A)(e_z x n) x m_b on x and y faces (kdx, kdy are zero when DMI
+// is off, which leaves the Neumann ghost m_b), m_b on z faces.
+__device__ __forceinline__ void neighbours(const float4* __restrict__ m, const Grid& g, const LocalCoef& c, int i,
+                                           int j, int k, long idx, float3 mc, float3& xp, float3& xm, float3& yp,
+                                           float3& ym, float3& zp, float3& zm) {
   const long sx = 1, sy = g.nx, sz = (long)g.nx * g.ny;
-  float3 xm, xp, ym, yp, zm, zp;
-  // chiral ghosts (kdx, kdy are zero when DMI is off)
   xp = (i + 1 < g.nx) ? f3(__ldg(&m[idx + sx])) : make_float3(mc.x - c.kdx * mc.z, mc.y, mc.z + c.kdx * mc.x);
   xm = (i > 0) ? f3(__ldg(&m[idx - sx])) : make_float3(mc.x + c.kdx * mc.z, mc.y, mc.z - c.kdx * mc.x);
   yp = (j + 1 < g.ny) ? f3(__ldg(&m[idx + sy])) : make_float3(mc.x, mc.y - c.kdy * mc.z, mc.z + c.kdy * mc.y);
   ym = (j > 0) ? f3(__ldg(&m[idx - sy])) : make_float3(mc.x, mc.y + c.kdy * mc.z, mc.z - c.kdy * mc.y);
   zp = (k + 1 < g.nz) ? f3(__ldg(&m[idx + sz])) : mc;
   zm = (k > 0) ? f3(__ldg(&m[idx - sz])) : mc;
+}
+
+// All field terms at cell (i, j, k); the demag term is the given value hdv.
+template <bool DMI>
+__device__ __forceinline__ void local_terms_v(const float4* __restrict__ m, float3 hdv, const Grid& g,
+                                              const LocalCoef& c, int i, int j, int k, long idx, float3 mc,
+                                              float inv_ms, Terms& t) {
+  float3 xm, xp, ym, yp, zm, zp;
+  neighbours(m, g, c, i, j, k, idx, mc, xp, xm, yp, ym, zp, zm);
   const float3 two = 2.f * mc;
   const float3 lap = c.inv_dx2 * (xp + xm - two) + c.inv_dy2 * (yp + ym - two) + c.inv_dz2 * (zp + zm - two);
   t.exch = (c.cA * inv_ms) * lap;
@@ -49,7 +59,15 @@ __device__ __forceinline__ void local_terms(const float4* __restrict__ m, const 
   const float cK = c.ku_map ? (__ldg(&c.ku_map[idx]) * (float)(2.0 / kMu0)) : c.cK;
   t.anis = (cK * inv_ms * dot3(mc, e)) * e;
   t.zee = make_float3(c.hx, c.hy, c.hz);
-  t.demag = hd ? f3(__ldg(&hd[idx])) : make_float3(0.f, 0.f, 0.f);
+  t.demag = hdv;
+}
+
+// All field terms at cell (i, j, k), the demag term read from hd (zero if hd is null).
+template <bool DMI>
+__device__ __forceinline__ void local_terms(const float4* __restrict__ m, const float4* __restrict__ hd,
+                                            const Grid& g, const LocalCoef& c, int i, int j, int k, long idx,
+                                            float3 mc, float inv_ms, Terms& t) {
+  local_terms_v<DMI>(m, hd ? f3(__ldg(&hd[idx])) : make_float3(0.f, 0.f, 0.f), g, c, i, j, k, idx, mc, inv_ms, t);
 }
 
 __device__ __forceinline__ float3 llg(const LocalCoef& c, float3 mc, float3 H) {
@@ -70,6 +88,50 @@ __device__ __forceinline__ float3 unit_norm(float3 v, float& r) {
   r = norm3df(v.x, v.y, v.z);
   const float inv = rnorm3df(v.x, v.y, v.z);
   return inv * v;
+}
+
+// One cell of the fused local stage: H_eff (demag term from io.hd), the LLG
+// right-hand side and the stage update of MODE (LocalMode), written to io.out.
+template <int MODE, bool DMI>
+__device__ __forceinline__ void local_cell(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j, int k,
+                                           long idx, int* flag) {
+  const float3 mc = f3(io.m[idx]);
+  const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
+  const float inv_ms = 1.f / ms;
+  Terms t;
+  local_terms<DMI>(io.m, io.hd, g, c, i, j, k, idx, mc, inv_ms, t);
+  float3 out;
+  float wout = 0.f;  // |u| of a renormalised stage output (used by the adjoint)
+  if (MODE == LM_HEFF) {
+    out = make_float3(0.f, 0.f, 0.f);
+    if (io.terms & MX_TERM_DEMAG) out = out + t.demag;
+    if (io.terms & MX_TERM_EXCH) out = out + t.exch;
+    if (io.terms & MX_TERM_ANIS) out = out + t.anis;
+    if (io.terms & MX_TERM_DMI) out = out + t.dmi;
+    if (io.terms & MX_TERM_ZEEMAN) out = out + t.zee;
+  } else {
+    const float3 H = t.demag + t.exch + t.anis + t.dmi + t.zee;
+    const float3 kk = llg(c, mc, H);
+    if (MODE == LM_RHS) {
+      out = kk;
+    } else if (MODE == LM_EULER) {
+      out = unit_norm(mc + io.dt * kk, wout);
+    } else if (MODE == LM_RK4_S0) {
+      io.acc[idx] = make_float4(kk.x, kk.y, kk.z, 0.f);
+      out = unit_norm(mc + (0.5f * io.dt) * kk, wout);
+    } else {
+      const float3 m0 = f3(io.m0[idx]);
+      const float3 a = f3(io.acc[idx]);
+      if (MODE == LM_RK4_S3) {
+        out = unit_norm(m0 + (io.dt * (1.f / 6.f)) * (a + kk), wout);
+      } else {
+        io.acc[idx] = make_float4(a.x + 2.f * kk.x, a.y + 2.f * kk.y, a.z + 2.f * kk.z, 0.f);
+        out = unit_norm(m0 + ((MODE == LM_RK4_S1 ? 0.5f : 1.f) * io.dt) * kk, wout);
+      }
+    }
+  }
+  if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, kFlagNonfinite);
+  io.out[idx] = make_float4(out.x, out.y, out.z, wout);
 }
 
 }  // namespace mx

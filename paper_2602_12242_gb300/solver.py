@@ -133,6 +133,11 @@ class Context:
         e = L.mx_energy(self.h, m, stream)
         return dict(zip(("demag", "exch", "anis", "dmi", "zeeman"), e))
 
+    def exchange_energy_central(self, m, stream=None):
+        """Exchange energy with central-difference gradients (the tabulated form)."""
+        self._check(m)
+        return L.mx_exchange_energy_central(self.h, m, stream)
+
     def sync(self, stream=None):
         L.mx_sync(self.h, stream)
 
