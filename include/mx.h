@@ -78,6 +78,9 @@ typedef enum {
  *           split into BF16 hi + lo parts (three products, FP32 accumulation),
  *           relative error near 2^-16 per stage; needs the per-kx-plane path
  *           and Px/2 in {512, 1024} (MX_ERR_UNSUPPORTED otherwise)
+ *   mri_fast_ratio  fast step of MX_MRI as a fraction of dt (each slow
+ *           stage interval takes ceil(interval / ratio) equal fast steps);
+ *           0 selects 0.1 (Sec. III-C); must be in [0, 1]
  */
 typedef struct {
     int nx, ny, nz;
@@ -90,6 +93,7 @@ typedef struct {
     int demag;
     int demag_path;
     int fft_mode;
+    double mri_fast_ratio;
 } mx_params;
 
 /* Demag convolution schedules for mx_params.demag_path. */
@@ -108,8 +112,19 @@ enum {
     MX_TERM_ALL = 31
 };
 
-/* Integrators for mx_rk_step. */
-enum { MX_RK4 = 0, MX_EULER = 1 };
+/* Integrators for mx_rk_step.
+ *   MX_RK4    classical RK4 (Sec. III-B/C)
+ *   MX_EULER  forward Euler (Sec. II-D, III-E)
+ *   MX_MRI    explicit-explicit multirate infinitesimal step (Sec. II-C,
+ *             III-C): fast part = the exchange-driven LLG right-hand side,
+ *             slow part = demag + anisotropy + DMI + Zeeman; Knoth-Wolke
+ *             3-stage third-order method on both levels; the slow stage
+ *             differences (a_ij - a_{i-1,j}) f_slow(Y_j) / (c_i - c_{i-1})
+ *             force the fast problem on each stage interval, integrated with
+ *             fast steps of mri_fast_ratio x dt.  Three demag evaluations per
+ *             step; every fast stage input and step result renormalised.
+ *             Allocates 3 float4 fields at its first use (MX_ERR_OOM). */
+enum { MX_RK4 = 0, MX_EULER = 1, MX_MRI = 2 };
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *mx_last_error(void);

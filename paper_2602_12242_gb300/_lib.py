@@ -19,7 +19,7 @@ STATUS_NAMES = {0: "MX_OK", 1: "MX_ERR_INVALID_ARG", 2: "MX_ERR_CUDA", 3: "MX_ER
                 5: "MX_ERR_NONFINITE", 6: "MX_ERR_TIMEOUT", 7: "MX_ERR_UNSUPPORTED"}
 MX_TERM_DEMAG, MX_TERM_EXCH, MX_TERM_ANIS, MX_TERM_DMI, MX_TERM_ZEEMAN = 1, 2, 4, 8, 16
 MX_TERM_ALL = 31
-MX_RK4, MX_EULER = 0, 1
+MX_RK4, MX_EULER, MX_MRI = 0, 1, 2
 MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE = 0, 1, 2
 MX_FFT_FP32, MX_FFT_SPLIT_BF16 = 0, 1
 
@@ -37,7 +37,7 @@ class mx_params(ctypes.Structure):
                 ("D", ctypes.c_double), ("alpha", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("ku_axis", ctypes.c_double * 3), ("h_bias", ctypes.c_double * 3),
                 ("dmi_interfacial", ctypes.c_int), ("precession", ctypes.c_int), ("demag", ctypes.c_int),
-                ("demag_path", ctypes.c_int), ("fft_mode", ctypes.c_int)]
+                ("demag_path", ctypes.c_int), ("fft_mode", ctypes.c_int), ("mri_fast_ratio", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

@@ -17,7 +17,7 @@ void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
 
 static const char* kNames[KID_COUNT] = {"x_fwd", "yz_fused", "y_fwd", "z_mul", "y_inv", "x_inv",
-                                        "local_stage", "normalize", "copy"};
+                                        "local_stage", "normalize", "copy", "mri_slow", "mri_fast"};
 const char* kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kNames[id] : ""; }
 
 // ---------------------------------------------------------------------------
@@ -107,6 +107,7 @@ static std::vector<float2> twiddles32(int L) {
 // One time step on stream st.  m is the caller's field (step start, updated
 // in place).
 static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cudaStream_t st) {
+  if (method == MX_MRI) return mri_step(ctx, m, dt, st);
   const bool demag = ctx->p.demag != 0;
   float4* hd = demag ? ctx->hd : nullptr;
   if (method == MX_EULER) {
@@ -171,6 +172,10 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 2048 || p->ny > 2048 || p->nz > 2048) {
     set_error("mx_create: grid must be 1..2048 cells per axis");
     return MX_ERR_UNSUPPORTED;
+  }
+  if (!(p->mri_fast_ratio >= 0.0 && p->mri_fast_ratio <= 1.0)) {
+    set_error("mx_create: mri_fast_ratio must be in [0, 1] (0: 0.1)");
+    return MX_ERR_INVALID_ARG;
   }
   if (!(p->dx > 0 && p->dy > 0 && p->dz > 0) || !(p->Ms > 0) || !(p->A >= 0) || !(p->alpha >= 0) ||
       !(p->gamma > 0) || !(p->Ku == p->Ku) || !(p->D == p->D)) {
@@ -266,7 +271,7 @@ mx_status mx_destroy(mx_ctx* ctx) {
   invalidate_graph(ctx);
   adjoint_free(ctx);
   void* ptrs[] = {ctx->ms_map, ctx->ku_map, ctx->axis_map, ctx->nhat, ctx->w1, ctx->w2, ctx->tw_x, ctx->tw_m, ctx->tw_mk, ctx->tw_yh, ctx->tw_y,
-                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered, ctx->red2, ctx->dft_a};
+                  ctx->tw_z, ctx->t_real, ctx->hd, ctx->sa, ctx->sb, ctx->acc, ctx->flag, ctx->ered, ctx->red2, ctx->dft_a, ctx->mri_f};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -396,8 +401,8 @@ mx_status mx_llg_rhs(mx_ctx* ctx, const float* m, float* dmdt, mx_stream_t strea
 static mx_status check_step_args(mx_ctx* ctx, const float* m, int nsteps, double dt, int method) {
   MX_TRY(check_ctx(ctx));
   MX_TRY(check_vec_ptr(m, "mx_rk_step: m"));
-  if (nsteps < 0 || !(dt > 0) || !isfinite(dt) || (method != MX_RK4 && method != MX_EULER)) {
-    set_error("mx_rk_step: need nsteps >= 0, finite dt > 0, method MX_RK4 or MX_EULER");
+  if (nsteps < 0 || !(dt > 0) || !isfinite(dt) || (method != MX_RK4 && method != MX_EULER && method != MX_MRI)) {
+    set_error("mx_rk_step: need nsteps >= 0, finite dt > 0, method MX_RK4, MX_EULER or MX_MRI");
     return MX_ERR_INVALID_ARG;
   }
   if (ctx->p.demag && !ctx->built && !ctx->surrogate) {
@@ -411,6 +416,7 @@ mx_status mx_rk_step(mx_ctx* ctx, float* m, int nsteps, double dt, int method, m
   MX_TRY(check_step_args(ctx, m, nsteps, dt, method));
   cudaStream_t st = (cudaStream_t)stream;
   if (nsteps == 0) return MX_OK;
+  if (method == MX_MRI) MX_TRY(mri_reserve(ctx));
   MX_TRY(normalize_field(ctx, (float4*)m, st));
   if (!ctx->graph || ctx->graph_m != m || ctx->graph_dt != dt || ctx->graph_method != method) {
     invalidate_graph(ctx);

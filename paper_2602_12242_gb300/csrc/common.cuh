@@ -168,5 +168,6 @@ struct mx_ctx {
 
   // learned demag backend (mx_set_demag_surrogate); NULL: FFT convolution
   struct mx_cnn* surrogate = nullptr;
+  float4* mri_f = nullptr;        // MRI slow right-hand sides F_1..F_3 (allocated at first use)
   double* red2 = nullptr;         // 2 FP64 accumulators for mx_rel_l2
 };

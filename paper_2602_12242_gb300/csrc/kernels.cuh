@@ -16,6 +16,8 @@ enum KernelId {
   KID_LOCAL,
   KID_NORMALIZE,
   KID_COPY,
+  KID_MRI_SLOW,
+  KID_MRI_FAST,
   KID_COUNT
 };
 const char* kernel_name(int id);
@@ -79,6 +81,10 @@ LocalCoef local_coef(const mx_ctx* ctx);
 mx_status local_stage(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st);
 mx_status normalize_field(mx_ctx* ctx, float4* m, cudaStream_t st);
 mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t st);
+// One explicit-explicit MRI step (mri.cu); mri_reserve allocates its slow
+// right-hand sides (call before a graph capture).
+mx_status mri_step(mx_ctx* ctx, float4* m, double dt, cudaStream_t st);
+mx_status mri_reserve(mx_ctx* ctx);
 mx_status energy_terms(mx_ctx* ctx, const float4* m, const float4* hd, double* e_dev, cudaStream_t st);
 mx_status exchange_energy_central(mx_ctx* ctx, const float4* m, double* e_dev, cudaStream_t st);
 

@@ -20,6 +20,12 @@ trajectory: snapshots of m every --every RK4 steps of a workload from its
 
 fft-mode timing: per-kernel time of the bulk RK4 step with FP32 x transforms
   and with the split-BF16 DFT-as-GEMM first x stage.
+
+  python -m paper_2602_12242_gb300.patterns --mri
+
+mri: time to solution of RK4 and of the explicit-explicit MRI step on the SP4
+  film with the stiffened 0.78125 nm grid (640x160x4), MRI at 5x the RK4 step,
+  both against a fine RK4 reference.
 """
 import argparse
 import json
@@ -139,6 +145,43 @@ def fft_mode_timing(name="bulk", steps=20):
     return out
 
 
+def mri_report(T=5e-11, dt_rk4=2e-14, mri_factor=5, ref_factor=4):
+    """Time to solution of RK4 and of the explicit-explicit MRI step over the
+    same interval T on the SP4 film with the stiffened 0.78125 nm grid of
+    Sec. III-C (640 x 160 x 4 cubic cells, Ms 8e5, A 1.3e-11, alpha 0.02,
+    field (-24.6, 4.3, 0) mT, initial m along (1, 0.25, 0.1) plus 1% seeded
+    noise): RK4 at dt_rk4, MRI at mri_factor x dt_rk4, both against RK4 at
+    dt_rk4 / ref_factor."""
+    h = 0.78125e-9
+    mu0 = 4e-7 * np.pi
+    cfg = dict(nx=640, ny=160, nz=4, dx=h, dy=h, dz=h, Ms=8e5, A=1.3e-11, Ku=0.0, ku_axis=(0.0, 0.0, 1.0), D=0.0,
+               dmi=False, alpha=0.02, gamma=2.211e5, h_bias=(-24.6e-3 / mu0, 4.3e-3 / mu0, 0.0))
+    m0 = inputs.near_uniform((4, 160, 640), (1.0, 0.25, 0.1), 0.01, 7)
+    out = {"grid": "640x160x4, 0.78125 nm", "T_s": T}
+    runs = {"rk4_ref": ("rk4", dt_rk4 / ref_factor), "rk4": ("rk4", dt_rk4), "mri": ("mri", dt_rk4 * mri_factor)}
+    res = {}
+    for name, (method, dt) in runs.items():
+        ctx = Context.from_config(cfg)
+        m = to_dev4(m0)
+        n = int(round(T / dt))
+        ctx.rk_step(m, 1, dt, method)  # capture the step graph outside the timed region
+        torch.cuda.synchronize()
+        m = to_dev4(m0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.rk_step(m, n, dt, method)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.sync()
+        res[name] = m[..., :3].double().clone()
+        out[name] = {"dt_s": dt, "steps": n, "ms": round(e0.elapsed_time(e1), 2)}
+        ctx.close()
+    for name in ("rk4", "mri"):
+        out[name]["max_err_vs_ref"] = float((res[name] - res["rk4_ref"]).abs().max())
+    out["mri_speedup_vs_rk4"] = round(out["rk4"]["ms"] / out["mri"]["ms"], 3)
+    return out
+
+
 def trajectory(name, steps, every):
     """m (float32, (n_snap, nz, ny, nx, 3)) at steps 0, every, 2 every, ... of
     a workload's RK4 run from its seeded initial state, and those step counts."""
@@ -166,6 +209,7 @@ def main():
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--npz", default=None)
     ap.add_argument("--fft-mode-timing", action="store_true")
+    ap.add_argument("--mri", action="store_true")
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--batch", type=int, default=128)
@@ -174,6 +218,9 @@ def main():
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    if a.mri:
+        print(json.dumps(mri_report()), flush=True)
+        return
     if a.fft_mode_timing:
         print(json.dumps(fft_mode_timing()), flush=True)
         return

@@ -22,12 +22,16 @@ def from_dev4(t):
     return t[..., :3].double().cpu().numpy()
 
 
+_METHODS = {"rk4": L.MX_RK4, "euler": L.MX_EULER, "mri": L.MX_MRI}
+
+
 class Context:
     """One simulation grid: parameters, demag kernel and workspaces on one GPU."""
 
     def __init__(self, nx, ny, nz, dx, dy, dz, Ms=8e5, A=1.3e-11, Ku=0.0, D=0.0, alpha=0.5,
                  gamma=2.211e5, ku_axis=(0.0, 0.0, 1.0), h_bias=(0.0, 0.0, 0.0), dmi=False,
-                 precession=True, demag=True, demag_path=0, fft_mode=0, build=True, stream=None):
+                 precession=True, demag=True, demag_path=0, fft_mode=0, mri_fast_ratio=0.0, build=True,
+                 stream=None):
         p = L.mx_params()
         p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
         p.dx, p.dy, p.dz = float(dx), float(dy), float(dz)
@@ -38,6 +42,7 @@ class Context:
         p.dmi_interfacial, p.precession, p.demag = int(bool(dmi)), int(bool(precession)), int(bool(demag))
         p.demag_path = int(demag_path)
         p.fft_mode = int(fft_mode)
+        p.mri_fast_ratio = float(mri_fast_ratio)
         self.params = p
         self.shape = (int(nz), int(ny), int(nx))
         self.h = None
@@ -125,7 +130,7 @@ class Context:
 
     def rk_step(self, m, nsteps, dt, method="rk4", stream=None):
         self._check(m)
-        L.mx_rk_step(self.h, m, nsteps, dt, L.MX_RK4 if method == "rk4" else L.MX_EULER, stream)
+        L.mx_rk_step(self.h, m, nsteps, dt, _METHODS[method], stream)
         return m
 
     def energy(self, m, stream=None):
@@ -158,7 +163,7 @@ class Context:
 
     def profile_step(self, m, nsteps, dt, method="rk4", stream=None):
         self._check(m)
-        return L.mx_profile_step(self.h, m, nsteps, dt, L.MX_RK4 if method == "rk4" else L.MX_EULER, stream)
+        return L.mx_profile_step(self.h, m, nsteps, dt, _METHODS[method], stream)
 
     # -- adjoint ---------------------------------------------------------------
     def adjoint_reserve(self, nsteps, checkpoint_every):

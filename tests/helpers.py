@@ -23,11 +23,11 @@ def problem(cfg, Ms=None, Ku=None, axis=None, demag=True, precession=True):
                       precession=precession)
 
 
-def context(cfg, Ms=None, Ku=None, axis=None, demag=True, demag_path=0, fft_mode=0):
+def context(cfg, Ms=None, Ku=None, axis=None, demag=True, demag_path=0, fft_mode=0, **kw):
     from paper_2602_12242_gb300.solver import Context
     c = dict(cfg)
     return Context.from_config(c, Ms=Ms, Ku=Ku, ku_axis=axis, demag=demag, demag_path=demag_path,
-                               fft_mode=fft_mode)
+                               fft_mode=fft_mode, **kw)
 
 
 def rel_l2(a, b):
