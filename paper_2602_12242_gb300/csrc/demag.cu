@@ -301,6 +301,8 @@ mx_status demag_setup(mx_ctx* ctx) {
   int T = kCap / (3 * g.Py * g.Pz);
   while (T > 1 && (size_t)3 * g.Py * g.Pz * T * sizeof(float2) > 96 * 1024) --T;
   if (T > 16) T = 16;
+  // fewer columns per block while that leaves fewer than two blocks per SM
+  while (T > 1 && (g.Hx + T - 1) / T < 2 * 152) T /= 2;
   ctx->fused_yz = ctx->p.demag_path == MX_DEMAG_AUTO && (T >= 1) && (3L * g.Py * g.Pz <= kCap) &&
                   (size_t)3 * g.Py * g.Pz * sizeof(float2) <= 96 * 1024;
   ctx->yz_tile = T < 1 ? 1 : T;

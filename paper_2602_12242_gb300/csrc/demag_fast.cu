@@ -144,23 +144,38 @@ static mx_status run_xi(mx_ctx* ctx, float4* hd, cudaStream_t st, bool setup) {
   return launch_check("xi_kernel");
 }
 
-// x pass for M = Px/2 (returns MX_ERR_UNSUPPORTED when no specialisation fits)
-static mx_status x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
-  const int M = ctx->g.Px / 2;
-#define MX_X(E_, S_, R_)                                                               \
-  return inverse ? run_xi<E_, S_, R_>(ctx, hd, st, setup) : run_xf<E_, S_, R_>(ctx, m, st, setup)
-  switch (M) {
-    case 1024: MX_X(32, 32, 2);
-    case 512: MX_X(32, 16, 4);
-    case 256: MX_X(16, 16, 4);
-    case 128: MX_X(16, 8, 8);
-    case 64: MX_X(8, 8, 8);
-    case 32: MX_X(32, 1, 32);
-    case 16: MX_X(16, 1, 32);
-    default: break;
+// x pass for M = Px/2 (returns MX_ERR_UNSUPPORTED when no specialisation fits).
+// Each size has a many-rows-per-block variant and a few-rows one; grids whose
+// row count would give fewer than two blocks per SM with the first take the
+// second (set-up prepares both).
+static constexpr int kMinBlocks = 2 * 152;
+
+template <int E, int S, int RB, int RS>
+static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
+  if (setup) {
+    mx_status s = run_xi<E, S, RB>(ctx, hd, st, true);
+    if (s == MX_OK) s = run_xf<E, S, RB>(ctx, m, st, true);
+    if (s == MX_OK) s = run_xi<E, S, RS>(ctx, hd, st, true);
+    if (s == MX_OK) s = run_xf<E, S, RS>(ctx, m, st, true);
+    return s;
   }
-#undef MX_X
-  return MX_ERR_UNSUPPORTED;
+  const int nrows = ctx->g.ny * ctx->g.nz;
+  if ((nrows + RB - 1) / RB >= kMinBlocks)
+    return inverse ? run_xi<E, S, RB>(ctx, hd, st, false) : run_xf<E, S, RB>(ctx, m, st, false);
+  return inverse ? run_xi<E, S, RS>(ctx, hd, st, false) : run_xf<E, S, RS>(ctx, m, st, false);
+}
+
+static mx_status x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
+  switch (ctx->g.Px / 2) {
+    case 1024: return x_pass_rs<32, 32, 2, 1>(ctx, m, hd, inverse, st, setup);
+    case 512: return x_pass_rs<32, 16, 4, 1>(ctx, m, hd, inverse, st, setup);
+    case 256: return x_pass_rs<16, 16, 4, 1>(ctx, m, hd, inverse, st, setup);
+    case 128: return x_pass_rs<16, 8, 8, 2>(ctx, m, hd, inverse, st, setup);
+    case 64: return x_pass_rs<8, 8, 8, 2>(ctx, m, hd, inverse, st, setup);
+    case 32: return x_pass_rs<32, 1, 32, 4>(ctx, m, hd, inverse, st, setup);
+    case 16: return x_pass_rs<16, 1, 32, 4>(ctx, m, hd, inverse, st, setup);
+    default: return MX_ERR_UNSUPPORTED;
+  }
 }
 
 mx_status fast_setup(mx_ctx* ctx) {
