@@ -236,8 +236,8 @@ mx_status mx_energy_noalloc(const mx_params *p, const float *m, const float *h_d
 
 /* Synchronise `stream`; return MX_ERR_NONFINITE (and clear the flag) if any
  * kernel of this context produced a NaN or Inf since the last mx_sync, or
- * MX_ERR_TIMEOUT if a bounded wait for a bulk copy in the demag kernel ran out
- * (its results are then invalid). */
+ * MX_ERR_TIMEOUT if a bounded wait (bulk copy of the demag kernel, tensor
+ * cores of an attached surrogate) ran out (results are then invalid). */
 mx_status mx_sync(mx_ctx *ctx, mx_stream_t stream);
 
 /* Padded grid of this context: out[0..2] = Px, Py, Pz. */
@@ -307,6 +307,11 @@ mx_status mx_cnn_forward(mx_cnn *net, const float *m, float *h, int batch, mx_st
  * mx_cnn_num_params floats) receive copies when not NULL. */
 mx_status mx_cnn_loss_grad(mx_cnn *net, const float *m, const float *h_target, int batch,
                            float *loss_out, float *grad_out, mx_stream_t stream);
+
+/* Synchronise `stream` and report the net's device status: MX_ERR_TIMEOUT
+ * (and clear it) if a bounded wait of a convolution kernel for its
+ * tensor-core MMAs ran out since the last call (results are then invalid). */
+mx_status mx_cnn_sync(mx_cnn *net, mx_stream_t stream);
 
 /* One Adam step with the last gradient: g += weight_decay * theta, then
  * the bias-corrected Adam update with learning rate lr. */

@@ -74,6 +74,7 @@ SIGNATURES = {
     "mx_cnn_set_normalizer": (_I, [_P, ctypes.POINTER(_D)]),
     "mx_cnn_forward": (_I, [_P, _P, _P, _I, _P]),
     "mx_cnn_loss_grad": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "mx_cnn_sync": (_I, [_P, _P]),
     "mx_cnn_adam_step": (_I, [_P, _D, _D, _P]),
     "mx_set_demag_surrogate": (_I, [_P, _P]),
     "mx_rel_l2": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
@@ -252,6 +253,10 @@ def mx_cnn_forward(net, m, h, batch, stream=None):
 def mx_cnn_loss_grad(net, m, h_target, batch, loss_out=None, grad_out=None, stream=None):
     check(lib().mx_cnn_loss_grad(net, ptr(m), ptr(h_target), int(batch), ptr(loss_out), ptr(grad_out),
                                  stream_handle(stream)))
+
+
+def mx_cnn_sync(net, stream=None):
+    check(lib().mx_cnn_sync(net, stream_handle(stream)))
 
 
 def mx_cnn_adam_step(net, lr, weight_decay, stream=None):

@@ -522,11 +522,16 @@ mx_status mx_sync(mx_ctx* ctx, mx_stream_t stream) {
   int flag = 0;
   MX_CUDA_TRY(cudaMemcpyAsync(&flag, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   MX_CUDA_TRY(cudaStreamSynchronize(st));
+  if (ctx->surrogate) {
+    int f = 0;
+    MX_TRY(cnn_take_flag(ctx->surrogate, st, &f));
+    flag |= f;
+  }
   if (flag) {
     MX_CUDA_TRY(cudaMemsetAsync(ctx->flag, 0, sizeof(int), st));
     MX_CUDA_TRY(cudaStreamSynchronize(st));
     if (flag & kFlagTimeout) {
-      set_error("mx_sync: a bounded wait for a bulk copy in the demag kernel ran out");
+      set_error("mx_sync: a bounded wait in a demag or surrogate kernel ran out");
       return MX_ERR_TIMEOUT;
     }
     set_error("mx_sync: a kernel produced a non-finite value");

@@ -7,11 +7,12 @@
 //
 // Activations are BF16, channels-last [b][z][y][x][C] with C padded to a
 // multiple of 16 (first input: 3 -> 16); weights are FP32 masters with BF16
-// copies for the tensor cores.  Every convolution is an implicit GEMM on
-// mma.sync m16n8k16 (BF16 in, FP32 accumulate): a block takes a 16 x 8 x 1
-// tile of output cells (one warp per row of 16 cells) and a (18 x 10 x 3)
-// halo of input cells staged with cp.async; all 27 taps of the layer's
-// weights stay in shared memory.
+// copies for the tensor cores.  Every convolution is an implicit GEMM on the
+// tcgen05 tensor cores (BF16 in, FP32 accumulator in tensor memory): a block
+// takes 8 x 16 x 1 tiles of output cells (M = 128) with a (10 x 18 x 3) halo
+// of input cells staged with cp.async; all 27 taps of the layer's weights
+// stay in shared memory.  The weight gradient is a split-K GEMM on
+// mma.sync m16n8k16.
 //   forward     out = conv(a, W) + b, stored pre-activation y and a = gelu(y)
 //   backward-x  dA_{l-1} = conv(dY_l, W'), W'[tap][ci][co] = W[26 - tap][co][ci],
 //               times gelu'(y_{l-1}) in the epilogue -> dY_{l-1}
@@ -26,7 +27,9 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "bulk.cuh"
 #include "mma.cuh"
+#include "tc05.cuh"
 
 namespace mx {
 
@@ -62,93 +65,164 @@ __host__ __device__ inline void tile_coords(const ConvDims& d, int t, int& b, in
 enum ConvMode { CM_HIDDEN = 0, CM_LAST = 1, CM_BWD = 2 };
 
 // ---------------------------------------------------------------------------
-// Convolution: in [cells][CIN] (bf16), weights wk [27][COUT][CIN] (bf16),
-// one persistent block per SM looping over tiles.
+// Convolution: in [cells][CIN] (bf16), weights wk [27][COUT][CIN] (bf16), on
+// the tcgen05 tensor cores, one persistent block per SM looping over tiles.
 //   CM_HIDDEN: ypre = acc + b (bf16), out = gelu(acc + b) (bf16), [cells][COUT]
 //   CM_LAST:   outf = acc + b (fp32) channels 0..2 of a float4 record per cell
-//   CM_BWD:    out = acc * gelu'(ypre) (bf16), [cells][COUT]  (ypre read)
+//   CM_BWD:    out = acc * gelu'(ypre) (bf16), [cells][COUT]  (ypre read)  A block (persistent, one
+// per SM) takes an 8 (x) x 16 (y) x 1 tile of output cells, M = 128 rows
+// (row = 8 y + x); N = COUT (16 for the last layer, whose padding rows are
+// zero weights); K = 27 taps x CIN.  Shared memory holds every operand in the
+// canonical K-major layout without swizzle:
+//   weights [tap][CIN/8][N][8]   B of tap t, K chunk c: 8-row groups (8 output
+//                                channels) 128 B apart, K chunks N x 16 B apart
+//   halo    [CIN/8][540][8]      (3 x 18 x 10 cells): A of tap (dz, dy, dx) starts
+//                                at cell (dz, dy, dx); consecutive x are 16 B
+//                                apart, so each output row y (8 cells) is one
+//                                8-row group and groups are 10 x 16 B apart
+// One thread issues the 27 CIN/16 MMAs of a tile into a TMEM accumulator
+// (128 lanes x N columns, FP32) and commits them to an mbarrier; after the
+// (bounded) wait, warp w reads lanes 32 (w mod 4) .. +31, columns of half
+// w / 4, for the epilogue.
 // ---------------------------------------------------------------------------
+constexpr int kTXc = 8, kTYc = 16;
+constexpr int kHXc = kTXc + 2, kHYc = kTYc + 2;
+constexpr int kHaloC = kHXc * kHYc * 3;
+
+template <int CIN, int COUT> struct ConvTc {
+  static constexpr int NP = COUT < 16 ? 16 : COUT;
+  static constexpr int KC = CIN / 8;
+  static constexpr size_t w_bytes = sizeof(bf16_t) * 8 * 27 * KC * NP;
+  static constexpr size_t h_bytes = sizeof(bf16_t) * 8 * KC * kHaloC;
+  // two halo buffers where they fit next to the weights (227 KB)
+  static constexpr int NB = (w_bytes + 2 * h_bytes <= 227 * 1024) ? 2 : 1;
+  static constexpr size_t smem = w_bytes + NB * h_bytes;
+  // two accumulators of NP columns, allocated as a power of two >= 32
+  static constexpr uint32_t TCOLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
+};
+
 template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(kCnnThreads, 1) conv_kernel(const bf16_t* __restrict__ in,
-                                                               const bf16_t* __restrict__ wk,
-                                                               const float* __restrict__ bias, bf16_t* __restrict__ out,
-                                                               bf16_t* __restrict__ ypre, float4* __restrict__ outf,
-                                                               ConvDims d) {
-  constexpr int CP = CIN + 8;   // smem pitch (elements) of a halo cell / weight row
-  constexpr int NT = COUT / 8;  // n tiles of 8
-  extern __shared__ __align__(16) unsigned char smraw[];
-  bf16_t* sw = (bf16_t*)smraw;                 // [27][COUT][CP]
-  bf16_t* sh = sw + 27 * COUT * CP;            // [kHalo][CP]
+__global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* __restrict__ in,
+                                                                  const bf16_t* __restrict__ wk,
+                                                                  const float* __restrict__ bias,
+                                                                  bf16_t* __restrict__ out, bf16_t* __restrict__ ypre,
+                                                                  float4* __restrict__ outf, ConvDims d, int* flag) {
+  typedef ConvTc<CIN, COUT> T;
+  constexpr int NP = T::NP, KC = T::KC, NH = NP / 2, NB = T::NB;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tbase;
+  bf16_t* sw = (bf16_t*)smraw;  // [27][KC][NP][8]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // weights: 27*COUT rows of CIN, 16-byte chunks
-  for (int e = tid; e < 27 * COUT * (CIN / 8); e += kCnnThreads) {
-    const int row = e / (CIN / 8), ch = e % (CIN / 8);
-    cp_async16(smem_u32(sw + row * CP + ch * 8), wk + (long)row * CIN + ch * 8, true);
+  for (int e = tid; e < 27 * KC * NP; e += kCnnThreads) {
+    const int co = e % NP, kc = (e / NP) % KC, tap = e / (NP * KC);
+    const bool ok = co < COUT;
+    cp_async16(smem_u32(sw + (long)e * 8), wk + ((long)tap * COUT + (ok ? co : 0)) * CIN + kc * 8, ok);
   }
-  cp_async_wait_all();
-  __syncthreads();
+  if (warp == 0) tmem_alloc(&tbase, T::TCOLS);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  const uint32_t sw_a = smem_u32(sw);
+  const uint32_t sh_a0 = sw_a + (uint32_t)T::w_bytes;
+  constexpr uint32_t idesc = tc_idesc_bf16(128, NP);
+  const int tiles_x = (d.nx + kTXc - 1) / kTXc, tiles_y = (d.ny + kTYc - 1) / kTYc;
+  const int ntiles = tiles_x * tiles_y * d.nz * d.batch;
+  const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long plane = (long)d.nx * d.ny;
-  for (int t = blockIdx.x; t < d.ntiles; t += gridDim.x) {
+  // this thread's accumulator row: cell (cx, cy) of the tile; lane quarter, column half
+  const int row = 32 * (warp & 3) + lane;
+  const int cx = row & 7, cy = row >> 3;
+  const int cb = (warp >> 2) * NH;
+  auto coords = [&](int k, int& b, int& z, int& y0, int& x0) {
+    const int t = blockIdx.x + k * gridDim.x;
+    const int tx = t % tiles_x;
+    int r = t / tiles_x;
+    const int ty = r % tiles_y;
+    r /= tiles_y;
+    z = r % d.nz;
+    b = r / d.nz;
+    x0 = tx * kTXc;
+    y0 = ty * kTYc;
+  };
+  // halo of tile k into buffer k % NB (cp.async, then visible to the tensor core)
+  auto load_halo = [&](int k) {
     int b, z, y0, x0;
-    tile_coords(d, t, b, z, y0, x0);
-    // halo cells (hz, hy, hx) -> input cell (z + hz - 1, y0 + hy - 1, x0 + hx - 1)
-    for (int e = tid; e < kHalo * (CIN / 8); e += kCnnThreads) {
-      const int hc = e / (CIN / 8), ch = e % (CIN / 8);
-      const int hx = hc % kHX, hy = (hc / kHX) % kHY, hz = hc / (kHX * kHY);
+    coords(k, b, z, y0, x0);
+    bf16_t* sh = (bf16_t*)(smraw + T::w_bytes + (k % NB) * T::h_bytes);
+    for (int e = tid; e < kHaloC * KC; e += kCnnThreads) {
+      const int hc = e % kHaloC, kc = e / kHaloC;
+      const int hx = hc % kHXc, hy = (hc / kHXc) % kHYc, hz = hc / (kHXc * kHYc);
       const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
       const bool ok = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 && gz < d.nz;
       const long cell = ok ? ((long)b * d.nz + gz) * plane + (long)gy * d.nx + gx : 0;
-      cp_async16(smem_u32(sh + hc * CP + ch * 8), in + cell * CIN + ch * 8, ok);
+      cp_async16(smem_u32(sh + (long)e * 8), in + cell * CIN + kc * 8, ok);
     }
     cp_async_wait_all();
-    __syncthreads();
-    float acc[NT][4];
-#pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    // A rows: cell (x = row, y = warp); ldmatrix lane -> (row, k half)
-    const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
-    const int akof = (lane >> 4) * 8;
+    fence_proxy_async_smem();
+  };
+  // the 27 CIN/16 MMAs of tile k into accumulator k & 1 (one thread)
+  auto issue = [&](int k) {
+    const uint32_t sh_a = sh_a0 + (uint32_t)((k % NB) * T::h_bytes);
+    const uint32_t dt = tbase + (uint32_t)((k & 1) * NP);
+    tc_fence_after_sync();
+#pragma unroll 1
     for (int tap = 0; tap < 27; ++tap) {
       const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-      const int hc = (dz * kHY + warp + dy) * kHX + arow + dx;
-      const bf16_t* arowp = sh + hc * CP + akof;
-      const bf16_t* wt = sw + tap * COUT * CP;
+      const uint32_t aoff = (uint32_t)(((dz * kHYc + dy) * kHXc + dx) * 16);
 #pragma unroll
-      for (int kc = 0; kc < CIN / 16; ++kc) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(smem_u32(arowp + kc * 16), a0, a1, a2, a3);
-#pragma unroll
-        for (int n = 0; n < NT; n += 2) {
-          if (n + 1 < NT) {
-            // two n tiles: lanes 0-7 (n, k0), 8-15 (n, k8), 16-23 (n+8, k0), 24-31 (n+8, k8)
-            const int wrow = n * 8 + (lane & 7) + ((lane >> 4) << 3);
-            const int wk8 = ((lane >> 3) & 1) * 8;
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4(smem_u32(wt + wrow * CP + kc * 16 + wk8), b0, b1, b2, b3);
-            mma16816(acc[n], a0, a1, a2, a3, b0, b1);
-            mma16816(acc[n + 1], a0, a1, a2, a3, b2, b3);
-          } else {
-            const int wrow = n * 8 + (lane & 7);
-            const int wk8 = ((lane >> 3) & 1) * 8;
-            uint32_t b0, b1;
-            ldsm_x2(smem_u32(wt + wrow * CP + kc * 16 + wk8), b0, b1);
-            mma16816(acc[n], a0, a1, a2, a3, b0, b1);
-          }
-        }
+      for (int ks = 0; ks < CIN / 16; ++ks) {
+        const uint64_t ad = tc_sdesc(sh_a + (uint32_t)(2 * ks * kHaloC * 16) + aoff, kHaloC * 16, kHXc * 16);
+        const uint64_t bd = tc_sdesc(sw_a + (uint32_t)((tap * KC + 2 * ks) * NP * 16), NP * 16, 128);
+        tc_mma_bf16(dt, ad, bd, idesc, tap > 0 || ks > 0);
       }
     }
-    // epilogue: thread holds rows g, g+8 (cells x0+g, x0+g+8 of row y0+warp), cols 8n + 2q, +1
-    const int g = lane >> 2, q = lane & 3;
-    const int gy = y0 + warp;
+    tc_commit(&bar[k & 1]);
+  };
+  uint32_t par[2] = {0u, 0u};
+  auto wait_mma = [&](int k) {
+    if (!mbar_wait(&bar[k & 1], par[k & 1])) atomicOr(flag, kFlagTimeout);
+    par[k & 1] ^= 1u;
+    tc_fence_after_sync();
+  };
+  cp_async_wait_all();  // weights
+  if (nmine > 0) load_halo(0);
+  tc_fence_before_sync();
+  __syncthreads();
+  if (nmine > 0 && tid == 0) issue(0);
+  for (int k = 0; k < nmine; ++k) {
+    bool waited = false;
+    if (k + 1 < nmine) {
+      if (NB == 1) {  // the only halo buffer is free once tile k's MMAs are done
+        wait_mma(k);
+        waited = true;
+      }
+      load_halo(k + 1);
+      tc_fence_before_sync();
+      __syncthreads();
+      if (tid == 0) issue(k + 1);
+    }
+    if (!waited) wait_mma(k);
+    // epilogue of tile k (overlaps the MMAs of tile k + 1)
+    float v[NH];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int gx = x0 + g + half * 8;
-      if (gx >= d.nx || gy >= d.ny) continue;
+    for (int q = 0; q < NH / 8; ++q) {
+      float t8[8];
+      tmem_ld8(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((k & 1) * NP + cb + 8 * q), t8);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[8 * q + i] = t8[i];
+    }
+    int b, z, y0, x0;
+    coords(k, b, z, y0, x0);
+    const int gx = x0 + cx, gy = y0 + cy;
+    if (gx < d.nx && gy < d.ny) {
       const long cell = ((long)b * d.nz + z) * plane + (long)gy * d.nx + gx;
 #pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const int c0 = n * 8 + 2 * q;
-        float v0 = acc[n][2 * half], v1 = acc[n][2 * half + 1];
+      for (int c = 0; c < NH; c += 2) {
+        const int c0 = cb + c;
+        if (c0 >= COUT) break;
+        float v0 = v[c], v1 = v[c + 1];
         if (MODE == CM_HIDDEN) {
           v0 += bias[c0];
           v1 += bias[c0 + 1];
@@ -165,7 +239,12 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_kernel(const bf16_t* __re
         }
       }
     }
-    __syncthreads();
+    tc_fence_before_sync();
+    __syncthreads();  // accumulator k & 1 and halo buffer k % NB may be reused
+  }
+  if (warp == 0) {
+    tc_fence_after_sync();
+    tmem_dealloc(tbase, T::TCOLS);
   }
 }
 
@@ -385,6 +464,7 @@ struct mx_cnn {
   bf16_t *dy4 = nullptr, *dy3 = nullptr, *dy2 = nullptr, *dy1 = nullptr;
   float4* pred = nullptr;
   float* loss = nullptr;
+  int* flag = nullptr;  // device status bits (kFlagTimeout), read by mx_cnn_sync / mx_sync
   float stats[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 1, 1, 1};
 };
 
@@ -409,19 +489,15 @@ static ConvDims conv_dims(const mx_cnn* n, int batch) {
   return d;
 }
 
-template <int CIN, int COUT, int MODE> static size_t conv_smem() {
-  return sizeof(bf16_t) * (27 * COUT + kHalo) * (CIN + 8);
-}
-
 static int g_num_sms = 0;
 
 template <int CIN, int COUT, int MODE>
 static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf16_t* out, bf16_t* ypre, float4* outf,
-                          const ConvDims& d, cudaStream_t st) {
-  const size_t sm = conv_smem<CIN, COUT, MODE>();
+                          const ConvDims& d, int* flag, cudaStream_t st) {
+  const size_t sm = ConvTc<CIN, COUT>::smem;
   static bool attr = false;
   if (!attr) {
-    MX_CUDA_TRY(cudaFuncSetAttribute(conv_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    MX_CUDA_TRY(cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sm));
     attr = true;
   }
@@ -431,9 +507,10 @@ static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf1
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 1;
   }
-  const int grid = d.ntiles < g_num_sms ? d.ntiles : g_num_sms;
-  conv_kernel<CIN, COUT, MODE><<<grid, kCnnThreads, sm, st>>>(in, w, b, out, ypre, outf, d);
-  return launch_check("conv_kernel");
+  const int ntiles = ((d.nx + kTXc - 1) / kTXc) * ((d.ny + kTYc - 1) / kTYc) * d.nz * d.batch;
+  const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+  conv_tc_kernel<CIN, COUT, MODE><<<grid, kCnnThreads, sm, st>>>(in, w, b, out, ypre, outf, d, flag);
+  return launch_check("conv_tc_kernel");
 }
 
 template <int CIN, int COUT>
@@ -470,10 +547,10 @@ static mx_status cnn_forward_to_pred(mx_cnn* n, const float4* m, int batch, cuda
   MX_TRY(launch_check("normalize_in_kernel"));
   const ConvDims d = conv_dims(n, batch);
   const float* P = n->params;
-  MX_TRY((conv_run<16, 32, CM_HIDDEN>(n->x0, n->wf[0], P + layer_w_off(0) + 32 * 3 * 27, n->a1, n->y1, nullptr, d, st)));
-  MX_TRY((conv_run<32, 64, CM_HIDDEN>(n->a1, n->wf[1], P + layer_w_off(1) + 64 * 32 * 27, n->a2, n->y2, nullptr, d, st)));
-  MX_TRY((conv_run<64, 32, CM_HIDDEN>(n->a2, n->wf[2], P + layer_w_off(2) + 32 * 64 * 27, n->a3, n->y3, nullptr, d, st)));
-  MX_TRY((conv_run<32, 8, CM_LAST>(n->a3, n->wf[3], P + layer_w_off(3) + 3 * 32 * 27, nullptr, nullptr, n->pred, d, st)));
+  MX_TRY((conv_run<16, 32, CM_HIDDEN>(n->x0, n->wf[0], P + layer_w_off(0) + 32 * 3 * 27, n->a1, n->y1, nullptr, d, n->flag, st)));
+  MX_TRY((conv_run<32, 64, CM_HIDDEN>(n->a1, n->wf[1], P + layer_w_off(1) + 64 * 32 * 27, n->a2, n->y2, nullptr, d, n->flag, st)));
+  MX_TRY((conv_run<64, 32, CM_HIDDEN>(n->a2, n->wf[2], P + layer_w_off(2) + 32 * 64 * 27, n->a3, n->y3, nullptr, d, n->flag, st)));
+  MX_TRY((conv_run<32, 8, CM_LAST>(n->a3, n->wf[3], P + layer_w_off(3) + 3 * 32 * 27, nullptr, nullptr, n->pred, d, n->flag, st)));
   return MX_OK;
 }
 
@@ -485,6 +562,19 @@ mx_status cnn_demag(mx_cnn* n, const float4* m, float4* h, cudaStream_t st) {
   denormalize_out_kernel<<<(unsigned)((n->cells + 255) / 256), 256, 0, st>>>(
       n->pred, h, n->cells, make_float3(s[6], s[7], s[8]), make_float3(s[9], s[10], s[11]));
   return launch_check("denormalize_out_kernel");
+}
+
+// Reads and clears the net's device status flag (synchronises `stream`).
+mx_status cnn_take_flag(mx_cnn* n, cudaStream_t st, int* flag_out) {
+  int f = 0;
+  MX_CUDA_TRY(cudaMemcpyAsync(&f, n->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MX_CUDA_TRY(cudaStreamSynchronize(st));
+  if (f) {
+    MX_CUDA_TRY(cudaMemsetAsync(n->flag, 0, sizeof(int), st));
+    MX_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  *flag_out = f;
+  return MX_OK;
 }
 
 }  // namespace mx
@@ -499,7 +589,7 @@ mx_status mx_cnn_destroy(mx_cnn* n) {
   if (!n) return MX_OK;
   void* ptrs[] = {n->params, n->grad, n->am, n->av, n->wf[0], n->wf[1], n->wf[2], n->wf[3], n->wb[1], n->wb[2],
                   n->wb[3], n->x0, n->a1, n->y1, n->a2, n->y2, n->a3, n->y3, n->dy4, n->dy3, n->dy2, n->dy1,
-                  n->pred, n->loss};
+                  n->pred, n->loss, n->flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete n;
@@ -550,12 +640,13 @@ mx_status mx_cnn_create(mx_cnn** out, int nx, int ny, int nz, int max_batch) {
   alloc((void**)&n->dy1, sizeof(bf16_t) * nc * 32);
   alloc((void**)&n->pred, sizeof(float4) * nc);
   alloc((void**)&n->loss, sizeof(float));
+  alloc((void**)&n->flag, sizeof(int));
   if (!ok) {
     mx_cnn_destroy(n);
     set_error("mx_cnn_create: device allocation failed");
     return MX_ERR_OOM;
   }
-  if (cudaMemset(n->params, 0, sizeof(float) * np) != cudaSuccess ||
+  if (cudaMemset(n->params, 0, sizeof(float) * np) != cudaSuccess || cudaMemset(n->flag, 0, sizeof(int)) != cudaSuccess ||
       cudaMemset(n->am, 0, sizeof(float) * np) != cudaSuccess ||
       cudaMemset(n->av, 0, sizeof(float) * np) != cudaSuccess) {
     mx_cnn_destroy(n);
@@ -563,6 +654,21 @@ mx_status mx_cnn_create(mx_cnn** out, int nx, int ny, int nz, int max_batch) {
     return MX_ERR_CUDA;
   }
   *out = n;
+  return MX_OK;
+}
+
+mx_status mx_cnn_sync(mx_cnn* n, mx_stream_t stream) {
+  clear_error();
+  if (!n) {
+    set_error("mx_cnn_sync: NULL net");
+    return MX_ERR_INVALID_ARG;
+  }
+  int f = 0;
+  MX_TRY(cnn_take_flag(n, (cudaStream_t)stream, &f));
+  if (f & kFlagTimeout) {
+    set_error("mx_cnn_sync: a bounded wait for the tensor cores ran out");
+    return MX_ERR_TIMEOUT;
+  }
   return MX_OK;
 }
 
@@ -652,17 +758,17 @@ mx_status mx_cnn_loss_grad(mx_cnn* n, const float* m, const float* h_target, int
   MX_TRY((wgrad_run<32, 16>(n->a3, n->dy4, G + layer_w_off(3), d, 32, 3, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy4, 16, 3, nc, G + layer_w_off(3) + 3 * 32 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
-  MX_TRY((conv_run<16, 32, CM_BWD>(n->dy4, n->wb[3], nullptr, n->dy3, n->y3, nullptr, d, st)));
+  MX_TRY((conv_run<16, 32, CM_BWD>(n->dy4, n->wb[3], nullptr, n->dy3, n->y3, nullptr, d, n->flag, st)));
   // layer 3
   MX_TRY((wgrad_run<64, 32>(n->a2, n->dy3, G + layer_w_off(2), d, 64, 32, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy3, 32, 32, nc, G + layer_w_off(2) + 32 * 64 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
-  MX_TRY((conv_run<32, 64, CM_BWD>(n->dy3, n->wb[2], nullptr, n->dy2, n->y2, nullptr, d, st)));
+  MX_TRY((conv_run<32, 64, CM_BWD>(n->dy3, n->wb[2], nullptr, n->dy2, n->y2, nullptr, d, n->flag, st)));
   // layer 2
   MX_TRY((wgrad_run<32, 64>(n->a1, n->dy2, G + layer_w_off(1), d, 32, 64, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy2, 64, 64, nc, G + layer_w_off(1) + 64 * 32 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
-  MX_TRY((conv_run<64, 32, CM_BWD>(n->dy2, n->wb[1], nullptr, n->dy1, n->y1, nullptr, d, st)));
+  MX_TRY((conv_run<64, 32, CM_BWD>(n->dy2, n->wb[1], nullptr, n->dy1, n->y1, nullptr, d, n->flag, st)));
   // layer 1
   MX_TRY((wgrad_run<16, 32>(n->x0, n->dy1, G + layer_w_off(0), d, 3, 32, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy1, 32, 32, nc, G + layer_w_off(0) + 32 * 3 * 27);

@@ -81,6 +81,9 @@ LocalCoef local_coef(const mx_ctx* ctx);
 mx_status local_stage(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st);
 mx_status normalize_field(mx_ctx* ctx, float4* m, cudaStream_t st);
 mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t st);
+// Reads and clears a conv net's device status flag (cnn.cu; synchronises st).
+mx_status cnn_take_flag(struct ::mx_cnn* n, cudaStream_t st, int* flag_out);
+
 // One explicit-explicit MRI step (mri.cu); mri_reserve allocates its slow
 // right-hand sides (call before a graph capture).
 mx_status mri_step(mx_ctx* ctx, float4* m, double dt, cudaStream_t st);
