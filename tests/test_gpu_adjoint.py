@@ -138,10 +138,16 @@ def _check_against_oracle(c, Ms, m0, patch, g, gms, nsteps, ndirs):
         dm = np.zeros(m0.shape)
         dm[idx] = 1.0
         dirs.append((dm, None))
+    # a directional derivative can nearly cancel along a random direction, so
+    # its error is bounded relative to |g_ref| |d| (Cauchy-Schwarz), the same
+    # 1e-3 bar as the relative L2 check above
+    # (in the coordinates (m0, Ms / 1e6) of the directions: gradient (g_m, 1e6 g_Ms))
+    gnorm = float(np.sqrt((g_ref.numpy() ** 2).sum() + ((1e6 * gms_ref.numpy()) ** 2).sum()))
     for dm, ds in dirs:
         fd = oadj.central_fd(p, m0, c["dt"], nsteps, obj, direction_m=dm, direction_ms=ds, h=1e-4)
         an = float((g * dm).sum() + (0.0 if ds is None else (gms * ds).sum()))
-        assert abs(an - fd) <= TOL_GRAD * abs(fd), (an, fd)
+        dnorm = float(np.sqrt((dm ** 2).sum() + (0.0 if ds is None else ((ds * 1e-6) ** 2).sum())))
+        assert abs(an - fd) <= TOL_GRAD * gnorm * dnorm, (an, fd, gnorm, dnorm)
 
 
 def test_adjoint_workload_grid_200_steps():
