@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
     x0 = tx * kTXc;
     y0 = ty * kTYc;
   };
-  // halo of tile k into buffer k % NB (cp.async, then visible to the tensor core)
+  // halo of tile k into buffer k % NB: issue the cp.async copies as one group
+  // (halo_ready waits for them and makes them visible to the tensor core)
   auto load_halo = [&](int k) {
     int b, z, y0, x0;
     coords(k, b, z, y0, x0);
@@ -159,7 +160,10 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
       const long cell = ok ? ((long)b * d.nz + gz) * plane + (long)gy * d.nx + gx : 0;
       cp_async16(smem_u32(sh + (long)e * 8), in + cell * CIN + kc * 8, ok);
     }
-    cp_async_wait_all();
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto halo_ready = [&]() {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     fence_proxy_async_smem();
   };
   // the 27 CIN/16 MMAs of tile k into accumulator k & 1 (one thread)
@@ -187,23 +191,34 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
     tc_fence_after_sync();
   };
   cp_async_wait_all();  // weights
-  if (nmine > 0) load_halo(0);
+  if (nmine > 0) {
+    load_halo(0);
+    halo_ready();
+  }
   tc_fence_before_sync();
   __syncthreads();
   if (nmine > 0 && tid == 0) issue(0);
+  if (NB == 2 && nmine > 1) load_halo(1);  // buffer 1 is free: prefetch
   for (int k = 0; k < nmine; ++k) {
-    bool waited = false;
-    if (k + 1 < nmine) {
-      if (NB == 1) {  // the only halo buffer is free once tile k's MMAs are done
-        wait_mma(k);
-        waited = true;
+    if (NB == 2) {
+      if (k + 1 < nmine) {
+        halo_ready();  // tile k + 1's halo (prefetched) is in buffer (k + 1) % 2
+        tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0) issue(k + 1);
       }
-      load_halo(k + 1);
-      tc_fence_before_sync();
-      __syncthreads();
-      if (tid == 0) issue(k + 1);
+      wait_mma(k);  // buffer k % 2 and accumulator k & 1 are done with
+      if (k + 2 < nmine) load_halo(k + 2);  // lands during the epilogue
+    } else {
+      wait_mma(k);  // the only halo buffer is free once tile k's MMAs are done
+      if (k + 1 < nmine) {
+        load_halo(k + 1);
+        halo_ready();
+        tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0) issue(k + 1);
+      }
     }
-    if (!waited) wait_mma(k);
     // epilogue of tile k (overlaps the MMAs of tile k + 1)
     float v[NH];
 #pragma unroll
