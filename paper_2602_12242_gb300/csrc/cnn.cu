@@ -265,8 +265,11 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
 
 // ---------------------------------------------------------------------------
 // Weight gradient of one layer: dW[tap][co][ci] += sum_cells dY[cell][co] *
-// x[cell + off(tap)][ci].  Block (tap, chunk): M = COUT rows (16 per m tile),
-// N = CIN, K = cells.  dY is [cells][COUT] (COUT padded to 16), x [cells][CIN].
+// x[cell + off(tap)][ci].  Block (chunk of 16 x 8 tiles, dz): the nine taps of
+// one dz share an (18 x 10) halo plane of x and the tile's dY, loaded once per
+// tile; each warp owns (tap, 16-row co tile, 8-column ci tile) output tiles of
+// M = COUT (16 per m tile), N = CIN, K = cells (one 16-cell row per k step).
+// dY is [cells][COUT] (COUT padded to 16), x [cells][CIN].
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __restrict__ x, const bf16_t* __restrict__ dy,
@@ -274,12 +277,12 @@ __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __rest
                                                             int cout_real, int tiles_per_block) {
   constexpr int XP = CIN + 8, YP = COUT + 8;
   constexpr int MT = COUT / 16, NTL = CIN / 8;  // m tiles of 16, n tiles of 8
-  constexpr int TILES = MT * NTL;
+  constexpr int TILES = 9 * MT * NTL;           // (tap in the dz plane, m tile, n tile)
   constexpr int PER_WARP = (TILES + 7) / 8;
-  __shared__ __align__(16) bf16_t sx[kTX * kTY * XP];
+  constexpr int HXp = kTX + 2, HYp = kTY + 2;   // halo plane
+  __shared__ __align__(16) bf16_t sx[HXp * HYp * XP];
   __shared__ __align__(16) bf16_t sy[kTX * kTY * YP];
-  const int tap = blockIdx.y;
-  const int dz = tap / 9, ddy = (tap / 3) % 3, ddx = tap % 3;
+  const int dz = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float acc[PER_WARP][4];
 #pragma unroll
@@ -290,16 +293,17 @@ __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __rest
   for (int t = t0; t < t1; ++t) {
     int b, z, y0, x0;
     tile_coords(d, t, b, z, y0, x0);
-    for (int e = tid; e < kTX * kTY * (CIN / 8); e += kCnnThreads) {
+    const int gz = z + dz - 1;
+    // halo plane gz: cells (hy, hx) -> x cell (gz, y0 + hy - 1, x0 + hx - 1)
+    for (int e = tid; e < HXp * HYp * (CIN / 8); e += kCnnThreads) {
       const int c = e / (CIN / 8), ch = e % (CIN / 8);
-      const int cx = c % kTX, cy = c / kTX;
-      const int ox = x0 + cx, oy = y0 + cy;
-      const int gx = ox + ddx - 1, gy = oy + ddy - 1, gz = z + dz - 1;
-      const bool ok = ox < d.nx && oy < d.ny && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 &&
-                      gz < d.nz;
+      const int hx = c % HXp, hy = c / HXp;
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1;
+      const bool ok = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 && gz < d.nz;
       const long cell = ok ? ((long)b * d.nz + gz) * plane + (long)gy * d.nx + gx : 0;
       cp_async16(smem_u32(sx + c * XP + ch * 8), x + cell * CIN + ch * 8, ok);
     }
+    // dY of the tile's output cells (zero outside the grid, so those cells add nothing)
     for (int e = tid; e < kTX * kTY * (COUT / 8); e += kCnnThreads) {
       const int c = e / (COUT / 8), ch = e % (COUT / 8);
       const int ox = x0 + c % kTX, oy = y0 + c / kTX;
@@ -313,8 +317,12 @@ __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __rest
     for (int i = 0; i < PER_WARP; ++i) {
       const int tile = warp * PER_WARP + i;
       if (tile >= TILES) break;
-      const int mt = tile / NTL, nt = tile % NTL;
-      for (int kc = 0; kc < kTX * kTY / 16; ++kc) {
+      const int tap9 = tile / (MT * NTL), rem = tile % (MT * NTL);
+      const int mt = rem / NTL, nt = rem % NTL;
+      const int ddy = tap9 / 3, ddx = tap9 % 3;
+#pragma unroll 2
+      for (int kc = 0; kc < kTY; ++kc) {
+        // k step kc = output row y0 + kc (16 cells)
         // A = dY^T (co x cells): stored [cell][co] -> transposed loads
         uint32_t a0, a1, a2, a3;
         {
@@ -322,12 +330,13 @@ __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __rest
           const int mcol = mt * 16 + ((lane >> 3) & 1) * 8;
           ldsm_x4_t(smem_u32(sy + krow * YP + mcol), a0, a1, a2, a3);
         }
-        // B = x (cells x ci), col layout from row-major [cell][ci] by transposed loads
+        // B = x of the shifted cells: output cell (kc, cx) reads halo (kc + ddy, cx + ddx)
         uint32_t b0, b1;
         {
-          const int krow = kc * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
+          const int cx = (lane & 7) + ((lane >> 3) & 1) * 8;
+          const int hrow = (kc + ddy) * HXp + cx + ddx;
           uint32_t r0, r1, r2, r3;
-          ldsm_x4_t(smem_u32(sx + krow * XP + nt * 8), r0, r1, r2, r3);
+          ldsm_x4_t(smem_u32(sx + hrow * XP + nt * 8), r0, r1, r2, r3);
           b0 = r0;
           b1 = r1;
           (void)r2;
@@ -344,7 +353,8 @@ __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __rest
   for (int i = 0; i < PER_WARP; ++i) {
     const int tile = warp * PER_WARP + i;
     if (tile >= TILES) break;
-    const int mt = tile / NTL, nt = tile % NTL;
+    const int tap = dz * 9 + tile / (MT * NTL), rem = tile % (MT * NTL);
+    const int mt = rem / NTL, nt = rem % NTL;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int co = mt * 16 + g + (r >= 2 ? 8 : 0);
@@ -531,9 +541,10 @@ static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf1
 template <int CIN, int COUT>
 static mx_status wgrad_run(const bf16_t* x, const bf16_t* dy, float* dw, const ConvDims& d, int cin_real,
                            int cout_real, cudaStream_t st) {
-  int tpb = d.ntiles / 32;
+  // about 2 x 152 blocks over the three dz planes
+  int tpb = d.ntiles / 100;
   if (tpb < 1) tpb = 1;
-  dim3 grid((d.ntiles + tpb - 1) / tpb, 27);
+  dim3 grid((d.ntiles + tpb - 1) / tpb, 3);
   wgrad_kernel<CIN, COUT><<<grid, kCnnThreads, 0, st>>>(x, dy, dw, d, cin_real, cout_real, tpb);
   return launch_check("wgrad_kernel");
 }
