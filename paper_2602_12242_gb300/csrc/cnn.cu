@@ -313,15 +313,15 @@ __global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __rest
     }
     cp_async_wait_all();
     __syncthreads();
+    // k steps outer, the warp's output tiles inner: independent accumulators
+    for (int kc = 0; kc < kTY; ++kc) {
 #pragma unroll
-    for (int i = 0; i < PER_WARP; ++i) {
-      const int tile = warp * PER_WARP + i;
-      if (tile >= TILES) break;
-      const int tap9 = tile / (MT * NTL), rem = tile % (MT * NTL);
-      const int mt = rem / NTL, nt = rem % NTL;
-      const int ddy = tap9 / 3, ddx = tap9 % 3;
-#pragma unroll 2
-      for (int kc = 0; kc < kTY; ++kc) {
+      for (int i = 0; i < PER_WARP; ++i) {
+        const int tile = warp * PER_WARP + i;
+        if (tile >= TILES) break;
+        const int tap9 = tile / (MT * NTL), rem = tile % (MT * NTL);
+        const int mt = rem / NTL, nt = rem % NTL;
+        const int ddy = tap9 / 3, ddx = tap9 % 3;
         // k step kc = output row y0 + kc (16 cells)
         // A = dY^T (co x cells): stored [cell][co] -> transposed loads
         uint32_t a0, a1, a2, a3;
