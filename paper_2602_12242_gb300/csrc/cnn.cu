@@ -90,7 +90,7 @@ constexpr int kHXc = kTXc + 2, kHYc = kTYc + 2;
 constexpr int kHaloC = kHXc * kHYc * 3;
 
 template <int CIN, int COUT> struct ConvTc {
-  static constexpr int NP = COUT < 16 ? 16 : COUT;
+  static constexpr int NP = COUT < 16 ? 16 : COUT;  // MMA N
   static constexpr int KC = CIN / 8;
   static constexpr size_t w_bytes = sizeof(bf16_t) * 8 * 27 * KC * NP;
   static constexpr size_t h_bytes = sizeof(bf16_t) * 8 * KC * kHaloC;
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
                                                                   float4* __restrict__ outf, ConvDims d, int* flag) {
   typedef ConvTc<CIN, COUT> T;
   constexpr int NP = T::NP, KC = T::KC, NH = NP / 2, NB = T::NB;
+  const int cta = (int)blockIdx.x, ncta = (int)gridDim.x;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tbase;
@@ -129,14 +130,14 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
   constexpr uint32_t idesc = tc_idesc_bf16(128, NP);
   const int tiles_x = (d.nx + kTXc - 1) / kTXc, tiles_y = (d.ny + kTYc - 1) / kTYc;
   const int ntiles = tiles_x * tiles_y * d.nz * d.batch;
-  const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int nmine = cta < ntiles ? (ntiles - 1 - cta) / ncta + 1 : 0;
   const long plane = (long)d.nx * d.ny;
   // this thread's accumulator row: cell (cx, cy) of the tile; lane quarter, column half
   const int row = 32 * (warp & 3) + lane;
   const int cx = row & 7, cy = row >> 3;
   const int cb = (warp >> 2) * NH;
   auto coords = [&](int k, int& b, int& z, int& y0, int& x0) {
-    const int t = blockIdx.x + k * gridDim.x;
+    const int t = cta + k * ncta;
     const int tx = t % tiles_x;
     int r = t / tiles_x;
     const int ty = r % tiles_y;
@@ -233,24 +234,36 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
     const int gx = x0 + cx, gy = y0 + cy;
     if (gx < d.nx && gy < d.ny) {
       const long cell = ((long)b * d.nz + z) * plane + (long)gy * d.nx + gx;
+      // eight channels per 16-byte store
 #pragma unroll
-      for (int c = 0; c < NH; c += 2) {
-        const int c0 = cb + c;
-        if (c0 >= COUT) break;
-        float v0 = v[c], v1 = v[c + 1];
+      for (int c = 0; c < NH; c += 8) {
+        const int cg = cb + c;  // channel of v[c]
+        if (cg >= COUT) break;
         if (MODE == CM_HIDDEN) {
-          v0 += bias[c0];
-          v1 += bias[c0 + 1];
-          *(uint32_t*)(ypre + cell * COUT + c0) = pack2(v0, v1);
-          *(uint32_t*)(out + cell * COUT + c0) = pack2(gelu_f(v0), gelu_f(v1));
+          uint32_t yp[4], o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float v0 = v[c + 2 * j] + bias[cg + 2 * j], v1 = v[c + 2 * j + 1] + bias[cg + 2 * j + 1];
+            yp[j] = pack2(v0, v1);
+            o[j] = pack2(gelu_f(v0), gelu_f(v1));
+          }
+          *(uint4*)(ypre + cell * COUT + cg) = make_uint4(yp[0], yp[1], yp[2], yp[3]);
+          *(uint4*)(out + cell * COUT + cg) = make_uint4(o[0], o[1], o[2], o[3]);
         } else if (MODE == CM_BWD) {
-          const uint32_t yp = *(const uint32_t*)(ypre + cell * COUT + c0);
-          const float y0f = bf2f((bf16_t)(yp & 0xffff)), y1f = bf2f((bf16_t)(yp >> 16));
-          *(uint32_t*)(out + cell * COUT + c0) = pack2(v0 * gelu_grad(y0f), v1 * gelu_grad(y1f));
+          const uint4 y4 = *(const uint4*)(ypre + cell * COUT + cg);
+          const uint32_t yw[4] = {y4.x, y4.y, y4.z, y4.w};
+          uint32_t o[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float y0f = bf2f((bf16_t)(yw[j] & 0xffff)), y1f = bf2f((bf16_t)(yw[j] >> 16));
+            o[j] = pack2(v[c + 2 * j] * gelu_grad(y0f), v[c + 2 * j + 1] * gelu_grad(y1f));
+          }
+          *(uint4*)(out + cell * COUT + cg) = make_uint4(o[0], o[1], o[2], o[3]);
         } else {
           float* o = (float*)(outf + cell);
-          if (c0 < 3) o[c0] = v0 + bias[c0];
-          if (c0 + 1 < 3) o[c0 + 1] = v1 + bias[c0 + 1];
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (cg + j < 3) o[cg + j] = v[c + j] + bias[cg + j];
         }
       }
     }
@@ -517,15 +530,23 @@ static ConvDims conv_dims(const mx_cnn* n, int batch) {
 static int g_num_sms = 0;
 
 template <int CIN, int COUT, int MODE>
-static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf16_t* out, bf16_t* ypre, float4* outf,
-                          const ConvDims& d, int* flag, cudaStream_t st) {
+static mx_status conv_launch(const bf16_t* in, const bf16_t* w, const float* b, bf16_t* out, bf16_t* ypre,
+                             float4* outf, const ConvDims& d, int* flag, int ntiles, cudaStream_t st) {
   const size_t sm = ConvTc<CIN, COUT>::smem;
   static bool attr = false;
   if (!attr) {
-    MX_CUDA_TRY(cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
+  const int ctas = ntiles < g_num_sms ? ntiles : g_num_sms;
+  conv_tc_kernel<CIN, COUT, MODE><<<ctas, kCnnThreads, sm, st>>>(in, w, b, out, ypre, outf, d, flag);
+  return launch_check("conv_tc_kernel");
+}
+
+template <int CIN, int COUT, int MODE>
+static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf16_t* out, bf16_t* ypre, float4* outf,
+                          const ConvDims& d, int* flag, cudaStream_t st) {
   if (!g_num_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -533,9 +554,7 @@ static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf1
     if (g_num_sms <= 0) g_num_sms = 1;
   }
   const int ntiles = ((d.nx + kTXc - 1) / kTXc) * ((d.ny + kTYc - 1) / kTYc) * d.nz * d.batch;
-  const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-  conv_tc_kernel<CIN, COUT, MODE><<<grid, kCnnThreads, sm, st>>>(in, w, b, out, ypre, outf, d, flag);
-  return launch_check("conv_tc_kernel");
+  return conv_launch<CIN, COUT, MODE>(in, w, b, out, ypre, outf, d, flag, ntiles, st);
 }
 
 template <int CIN, int COUT>
