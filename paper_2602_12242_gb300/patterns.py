@@ -182,13 +182,18 @@ def mri_report(T=5e-11, dt_rk4=2e-14, mri_factor=5, ref_factor=4):
     return out
 
 
-def trajectory(name, steps, every):
+def trajectory(name, steps, every, perturb=False):
     """m (float32, (n_snap, nz, ny, nx, 3)) at steps 0, every, 2 every, ... of
-    a workload's RK4 run from its seeded initial state, and those step counts."""
+    a workload's RK4 run from its seeded initial state, and those step counts.
+    With ``perturb`` every component of m0 is scaled by 1 +- 2^-24 (seeded
+    signs): the run's own sensitivity to rounding-level changes."""
     cfg = dict(inputs.CONFIGS[name])
     Ms, Ku, axis = inputs.material(name)
     ctx = Context.from_config(cfg, Ms=Ms, Ku=Ku, ku_axis=axis)
-    m = to_dev4(inputs.initial_m(name))
+    m0 = inputs.initial_m(name)
+    if perturb:
+        m0 = m0 * (1.0 + 2.0 ** -24 * inputs.rng(99).choice([-1.0, 1.0], size=m0.shape))
+    m = to_dev4(m0)
     snaps, at = [m[..., :3].cpu().numpy().copy()], [0]
     done = 0
     while done < steps:
@@ -208,6 +213,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--every", type=int, default=1000)
     ap.add_argument("--npz", default=None)
+    ap.add_argument("--perturb", action="store_true")
     ap.add_argument("--fft-mode-timing", action="store_true")
     ap.add_argument("--mri", action="store_true")
     ap.add_argument("--pairs", type=int, default=20000)
@@ -225,7 +231,7 @@ def main():
         print(json.dumps(fft_mode_timing()), flush=True)
         return
     if a.trajectory:
-        snaps, at = trajectory(a.trajectory, a.steps, a.every)
+        snaps, at = trajectory(a.trajectory, a.steps, a.every, a.perturb)
         np.savez_compressed(a.npz or f"{a.trajectory}_fp32.npz", m=snaps, step=at)
         return
     rep = {"learned": learned_report(a.pairs, a.epochs, a.batch, a.insteps, a.judge)}
