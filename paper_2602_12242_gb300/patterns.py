@@ -37,7 +37,8 @@ import torch
 from . import _lib as L
 from . import inputs
 from .solver import Context, to_dev4
-from .surrogate import Surrogate, init_params, make_dataset, normalizer_stats, run_in_loop, time_demag, train
+from .surrogate import (Surrogate, init_params, make_dataset, normalizer_stats, run_in_loop, time_batched, time_demag,
+                        train)
 
 
 def _rk_time(ctx, m, n, dt):
@@ -72,6 +73,7 @@ def learned_report(pairs, epochs, batch, insteps, judge, holdout=64, log=print):
         errs.append(L.mx_rel_l2(ctx.h, net.forward(M[i]), H[i]))
     m_test = M[pairs].clone()
     tdem = time_demag(ctx, net, m_test)
+    tbatch = time_batched(ctx, net, M[pairs:pairs + holdout])
     # RK4 step time with each backend
     m1 = M[pairs].clone()
     t_fft = _rk_time(ctx, m1, 100, cfg["dt"])
@@ -96,7 +98,8 @@ def learned_report(pairs, epochs, batch, insteps, judge, holdout=64, log=print):
         "loss_first_last": [losses[0], losses[-1]],
         "holdout_rel_l2_mean": float(np.mean(errs)), "holdout_rel_l2_max": float(np.max(errs)),
         "untrained_rel_l2": err_untrained,
-        "demag_eval_ms": tdem, "rk4_step_ms": {"fft": t_fft, "surrogate": t_sur},
+        "demag_eval_ms": tdem, "batched_demag_ms_per_field": tbatch,
+        "rk4_step_ms": {"fft": t_fft, "surrogate": t_sur},
         "in_loop": {"steps": insteps, "judge_every": judge, "threshold": 1e-2,
                     "fallback_step": res["fallback_step"], "first_errors": res["errors"][:5],
                     "free_run_errors": res_free["errors"][:: max(1, len(res_free["errors"]) // 10)],

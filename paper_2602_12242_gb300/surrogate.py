@@ -162,6 +162,36 @@ def run_in_loop(ctx, net, m, nsteps, dt, judge_every, threshold=1e-2):
     return {"errors": errors, "fallback_step": fallback}
 
 
+def time_batched(ctx, net, M, reps=10):
+    """Per-field time [ms] of demag fields for a batch of fields: the FFT
+    convolution one field after another, and one batched surrogate forward
+    (the net's max_batch fields at once)."""
+    b = min(net.max_batch, M.shape[0])
+    h = torch.empty_like(M[:b])
+    out = {}
+    for name in ("fft", "surrogate"):
+        for _ in range(2):
+            if name == "fft":
+                for i in range(b):
+                    ctx.heff(M[i], out=h[i], terms=L.MX_TERM_DEMAG)
+            else:
+                L.mx_cnn_forward(net.h, M[:b].contiguous(), h, b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            if name == "fft":
+                for i in range(b):
+                    ctx.heff(M[i], out=h[i], terms=L.MX_TERM_DEMAG)
+            else:
+                L.mx_cnn_forward(net.h, M[:b].contiguous(), h, b)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / (reps * b)
+    out["batch"] = b
+    return out
+
+
 def time_demag(ctx, net, m, reps=50):
     """Mean time [ms] of one demag evaluation by the FFT convolution and by the surrogate."""
     h = torch.empty_like(m)

@@ -124,3 +124,22 @@ def test_training_reduces_loss_and_in_loop_fallback():
     m2 = M[1].clone()
     res2 = run_in_loop(ctx, net, m2, nsteps=6, dt=1e-14, judge_every=3, threshold=10.0)
     assert res2["fallback_step"] is None and len(res2["errors"]) == 2
+
+
+def test_batched_surrogate_cost_per_field_against_fft():
+    """What the network gains over the method without it, in time: demag
+    fields for a batch of 64 textures of 64x64x4 cells, by the FFT convolution
+    field by field and by one batched surrogate forward.  The batched network
+    must cost less per field (its accuracy is the separate held-out check)."""
+    from paper_2602_12242_gb300 import inputs
+    from paper_2602_12242_gb300.solver import to_dev4
+    from paper_2602_12242_gb300.surrogate import Surrogate, time_batched
+    c = dict(inputs.CONFIGS["learned"])
+    ctx = context(c)
+    M = torch.stack([to_dev4(inputs.smooth_texture((4, 64, 64), 8.0, 7000 + i)) for i in range(64)])
+    net = Surrogate(64, 64, 4, max_batch=64)
+    net.set_params(torch.as_tensor(ocnn.init_params(5), dtype=torch.float32))
+    net.set_normalizer(STATS)
+    t = time_batched(ctx, net, M, reps=5)
+    print(f"\nper-field demag time, batch {t['batch']}: FFT {1e3 * t['fft']:.1f} us, surrogate {1e3 * t['surrogate']:.1f} us")
+    assert t["surrogate"] < t["fft"], t
