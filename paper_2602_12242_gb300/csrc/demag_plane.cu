@@ -8,16 +8,17 @@
 //
 //   xfk  r2c along x for R consecutive rows (same z); the spectrum is
 //        transposed in shared memory so the kx-major stores are coalesced.
-//   yzh  one block per kx: the y transform of the zero-padded column (only the
-//        first ny <= Py/2 inputs non-zero) splits into its even outputs, an
-//        Py/2-point FFT of x, and its odd outputs, an Py/2-point FFT of
-//        x W_Py^y.  The block runs the two halves one after the other; each
-//        holds [c][z][Py/2] in shared memory: forward y FFT, then per ky the
-//        z FFT, the 3x3 tensor multiply and the inverse z FFT (four lanes per
-//        column, one residue class kz mod 4 each), then the inverse y FFT.  The
-//        inverse y transform restricted to y < ny is the sum of the two
-//        halves' inverses, the odd one times W_Py^-y: the even half is stored
-//        and the odd half is added to it.
+//   yzh  a cluster of two CTAs per kx: the y transform of the zero-padded
+//        column (only the first ny <= Py/2 inputs non-zero) splits into its
+//        even outputs, an Py/2-point FFT of x, and its odd outputs, an
+//        Py/2-point FFT of x W_Py^y.  CTA h holds half h, [c][z][Py/2], in
+//        shared memory (bulk row copies in): forward y FFT, then per ky the z
+//        FFT, the 3x3 tensor multiply and the inverse z FFT (four lanes per
+//        column, one residue class kz mod 4 each), then the inverse y FFT.
+//        The inverse y transform restricted to y < ny is the sum of the two
+//        halves' inverses, the odd one times W_Py^-y: each CTA sums half of
+//        the plane's rows with the other CTA's rows (distributed shared
+//        memory) and bulk-stores them.
 //   xik  c2r along x for R consecutive rows, reading the kx-major spectrum.
 #include <math.h>
 
