@@ -136,6 +136,7 @@ struct mx_ctx {
   float2* tw_z = nullptr;         // W_Pz^k, k < Pz
   bool fused_yz = false;          // y/z passes in one kernel (plane fits on chip)
   bool fast_x = false;            // compile-time-sized x passes available
+  bool yz2d = false;              // single-z-plane y kernel (Pz == 1) for the fused y/z pass
   float2* tw_m = nullptr;         // W_M^k, k < M = Px/2
   float2* tw_mk = nullptr;        // W_M^(s k) at [k * S + s] for the plane path's x line FFTs (M = E S)
   float2* tw_yh = nullptr;        // W_{Py/2}^k, k < Py/2

@@ -334,7 +334,10 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
       MX_TRY(launch_check("x_fwd_kernel"));
     }
   }
-  if (ctx->fused_yz) {
+  if (ctx->yz2d) {
+    ProfScope ps(ctx, KID_YZ, st);
+    MX_TRY(yz2d_pass(ctx, st));
+  } else if (ctx->fused_yz) {
     const int T = ctx->yz_tile;
     const size_t s = sizeof(float2) * 3 * g.Py * g.Pz * T;
     ProfScope ps(ctx, KID_YZ, st);

@@ -114,6 +114,104 @@ __global__ void __launch_bounds__(3 * R * S) xi_kernel(const float2* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// y transform + tensor multiply + inverse y of a one-z-plane spectrum
+// (Pz == 1, so no z transform and N_xz = N_yz = 0), T kx columns per block,
+// small-grid layout w1[c][y][kx].  The Py-point transform of the zero-padded
+// column (inputs y < ny <= Py/2) splits into its even outputs, a Py/2-point
+// FFT of x, and its odd outputs, a Py/2-point FFT of x W_Py^y; the inverse
+// restricted to y < ny is even + W_Py^-y odd.  Lines (c, t, half) of LH =
+// Py/2 points run the register line FFT, S threads each.
+// ---------------------------------------------------------------------------
+template <int E, int S, int T>
+__global__ void __launch_bounds__(6 * T * S) yz2d_kernel(float2* __restrict__ w1, Grid g,
+                                                         const float* __restrict__ nhat,
+                                                         const float2* __restrict__ twH,
+                                                         const float2* __restrict__ twPy) {
+  constexpr int LH = E * S;
+  constexpr int PITCH = LineFft<E, S>::kPitch;
+  constexpr int NT = 6 * T * S;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* twS = sm + 6 * T * PITCH;  // W_LH^(s k) at [k S + s]
+  float2* twS2 = twS + LH;           // W_Py^y, y < LH
+  const int kx0 = blockIdx.x * T;
+  const int tid = threadIdx.x;
+  const int ny = g.ny;
+  const long wc = (long)g.ny * g.Hx;  // component stride of w1 (one z plane)
+  for (int q = tid; q < LH; q += NT) {
+    twS[q] = __ldg(&twH[(q % S) * (q / S)]);
+    twS2[q] = __ldg(&twPy[q]);
+  }
+  __syncthreads();
+  // line (c, t, h) at ((c T + t) 2 + h) PITCH
+  for (int e = tid; e < 3 * T * LH; e += NT) {
+    const int t = e % T, y = (e / T) % LH, c = e / (T * LH);
+    const int kx = kx0 + t;
+    float2 v = make_float2(0.f, 0.f);
+    if (y < ny && kx < g.Hx) v = w1[c * wc + (long)y * g.Hx + kx];
+    float2* L = sm + ((c * T + t) * 2) * PITCH;
+    L[y] = v;
+    L[PITCH + y] = cmul(v, twS2[y]);
+  }
+  __syncthreads();
+  line_fft<E, S, false, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
+  __syncthreads();
+  const long no = (long)g.Hx * g.Oy * g.Oz;
+  for (int e = tid; e < T * 2 * LH; e += NT) {
+    const int j = e % LH, h = (e / LH) % 2, t = e / (2 * LH);
+    const int kx = kx0 + t;
+    if (kx >= g.Hx) continue;
+    const int ky = 2 * j + h;
+    const bool fy = ky > (g.Py >> 1);
+    const long o = (long)(fy ? g.Py - ky : ky) * g.Hx + kx;
+    const float nxx = __ldg(&nhat[o]), nyy = __ldg(&nhat[no + o]), nzz = __ldg(&nhat[2 * no + o]);
+    const float nxy = (fy ? -1.f : 1.f) * __ldg(&nhat[3 * no + o]);
+    float2* px = sm + ((0 * T + t) * 2 + h) * PITCH + j;
+    float2* py = sm + ((1 * T + t) * 2 + h) * PITCH + j;
+    float2* pz = sm + ((2 * T + t) * 2 + h) * PITCH + j;
+    const float2 mx = *px, my = *py, mz = *pz;
+    *px = make_float2(nxx * mx.x + nxy * my.x, nxx * mx.y + nxy * my.y);
+    *py = make_float2(nxy * mx.x + nyy * my.x, nxy * mx.y + nyy * my.y);
+    *pz = make_float2(nzz * mz.x, nzz * mz.y);
+  }
+  __syncthreads();
+  line_fft<E, S, true, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
+  __syncthreads();
+  for (int e = tid; e < 3 * T * ny; e += NT) {
+    const int t = e % T, y = (e / T) % ny, c = e / (T * ny);
+    const int kx = kx0 + t;
+    if (kx >= g.Hx) continue;
+    const float2* L = sm + ((c * T + t) * 2) * PITCH;
+    w1[c * wc + (long)y * g.Hx + kx] = cadd(L[y], cmul(L[PITCH + y], cconj(twS2[y])));
+  }
+}
+
+template <int E, int S, int T>
+static mx_status yz2d_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
+  const size_t sm = sizeof(float2) * (6 * T * LineFft<E, S>::kPitch + 2 * E * S);
+  if (setup) {
+    MX_CUDA_TRY(cudaFuncSetAttribute(yz2d_kernel<E, S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    return MX_OK;
+  }
+  yz2d_kernel<E, S, T><<<(ctx->g.Hx + T - 1) / T, 6 * T * S, sm, st>>>(ctx->w1, ctx->g, ctx->nhat, ctx->tw_yh,
+                                                                      ctx->tw_y);
+  return launch_check("yz2d_kernel");
+}
+
+static mx_status yz2d_dispatch(mx_ctx* ctx, cudaStream_t st, bool setup) {
+  switch (ctx->g.Py / 2) {
+    case 512: return yz2d_run<32, 16, 2>(ctx, st, setup);
+    case 256: return yz2d_run<16, 16, 2>(ctx, st, setup);
+    case 128: return yz2d_run<16, 8, 2>(ctx, st, setup);
+    case 64: return yz2d_run<8, 8, 2>(ctx, st, setup);
+    case 32: return yz2d_run<32, 1, 8>(ctx, st, setup);
+    case 16: return yz2d_run<16, 1, 8>(ctx, st, setup);
+    default: return MX_ERR_UNSUPPORTED;
+  }
+}
+
+mx_status yz2d_pass(mx_ctx* ctx, cudaStream_t st) { return yz2d_dispatch(ctx, st, false); }
+
+// ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
 template <int E, int S> static size_t x_smem(int R) { return sizeof(float2) * 3 * R * LineFft<E, S>::kPitch; }
@@ -183,6 +281,7 @@ mx_status fast_setup(mx_ctx* ctx) {
   ctx->fast_x = ctx->p.demag_path != MX_DEMAG_GENERIC &&
                 x_pass(ctx, nullptr, nullptr, false, nullptr, true) == MX_OK &&
                 x_pass(ctx, nullptr, nullptr, true, nullptr, true) == MX_OK;
+  ctx->yz2d = ctx->fused_yz && ctx->g.Pz == 1 && yz2d_dispatch(ctx, nullptr, true) == MX_OK;
   clear_error();
   return MX_OK;
 }

@@ -38,6 +38,8 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
 
 // demag_fast.cu
 mx_status fast_setup(mx_ctx* ctx);
+// y transform, tensor multiply and inverse y of a one-z-plane spectrum (Pz == 1), in place on w1.
+mx_status yz2d_pass(mx_ctx* ctx, cudaStream_t st);
 mx_status fast_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st);
 
 // demag_plane.cu
