@@ -26,44 +26,71 @@ __global__ void __launch_bounds__(3 * R * S) xf_kernel(const float4* __restrict_
   const int nrows = g.ny * g.nz;
   const int row0 = blockIdx.x * R;
   const int tid = threadIdx.x;
-  for (int e = tid; e < R * M; e += NT) {
-    const int r = e / M, n = e % M;
-    const int row = row0 + r;
-    float2 zx = make_float2(0.f, 0.f), zy = zx, zz = zx;
-    if (row < nrows) {
-      const long cell = (long)row * g.nx;
-      const int i0 = 2 * n, i1 = i0 + 1;
-      if (i0 < g.nx) {
-        const float4 a = __ldg(&m[cell + i0]);
-        const float s = ms_map ? __ldg(&ms_map[cell + i0]) : ms;
-        zx.x = s * a.x; zy.x = s * a.y; zz.x = s * a.z;
-      }
-      if (i1 < g.nx) {
-        const float4 b = __ldg(&m[cell + i1]);
-        const float s = ms_map ? __ldg(&ms_map[cell + i1]) : ms;
-        zx.y = s * b.x; zy.y = s * b.y; zz.y = s * b.z;
+  // batches of kB cell pairs per thread: 2 kB independent loads in flight
+  constexpr int kB = 4;
+  for (int e0 = tid; e0 < R * M; e0 += NT * kB) {
+    float4 a[kB], b[kB];
+    float sa[kB], sb[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * NT;
+      const int r = e / M, n = e % M;
+      const int row = row0 + r;
+      a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      sa[u] = sb[u] = ms;
+      if (e < R * M && row < nrows) {
+        const long cell = (long)row * g.nx;
+        const int i0 = 2 * n, i1 = i0 + 1;
+        if (i0 < g.nx) {
+          a[u] = __ldg(&m[cell + i0]);
+          if (ms_map) sa[u] = __ldg(&ms_map[cell + i0]);
+        }
+        if (i1 < g.nx) {
+          b[u] = __ldg(&m[cell + i1]);
+          if (ms_map) sb[u] = __ldg(&ms_map[cell + i1]);
+        }
       }
     }
-    sm[(3 * r + 0) * P + n] = zx;
-    sm[(3 * r + 1) * P + n] = zy;
-    sm[(3 * r + 2) * P + n] = zz;
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * NT;
+      if (e >= R * M) break;
+      const int r = e / M, n = e % M;
+      // zero outside the grid (a, b are zero there)
+      sm[(3 * r + 0) * P + n] = make_float2(sa[u] * a[u].x, sb[u] * b[u].x);
+      sm[(3 * r + 1) * P + n] = make_float2(sa[u] * a[u].y, sb[u] * b[u].y);
+      sm[(3 * r + 2) * P + n] = make_float2(sa[u] * a[u].z, sb[u] * b[u].z);
+    }
   }
   __syncthreads();
   line_fft<E, S, false>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
   const long cs = (long)g.nz * g.ny * g.Hx;
-  for (int e = tid; e < 3 * R * (M + 1); e += NT) {
-    const int line = e / (M + 1), k = e % (M + 1);
-    const int r = line / 3, c = line % 3;
-    const int row = row0 + r;
-    if (row >= nrows) continue;
-    const float2* L = sm + line * P;
-    const float2 zk = L[k == M ? 0 : k];
-    const float2 zc = cconj(L[k == 0 ? 0 : M - k]);
-    const float2 Ev = cscale(cadd(zk, zc), 0.5f);
-    const float2 D = csub(zk, zc);
-    const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-    w1[c * cs + (long)row * g.Hx + k] = cadd(Ev, cmul(__ldg(&twP[k]), O));
+  // batches of kB outputs per thread: the twiddle loads of a batch go out together
+  constexpr int kBo = 4;
+  for (int e0 = tid; e0 < 3 * R * (M + 1); e0 += NT * kBo) {
+    float2 tw[kBo];
+#pragma unroll
+    for (int u = 0; u < kBo; ++u) {
+      const int e = e0 + u * NT;
+      tw[u] = e < 3 * R * (M + 1) ? __ldg(&twP[e % (M + 1)]) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kBo; ++u) {
+      const int e = e0 + u * NT;
+      if (e >= 3 * R * (M + 1)) break;
+      const int line = e / (M + 1), k = e % (M + 1);
+      const int r = line / 3, c = line % 3;
+      const int row = row0 + r;
+      if (row >= nrows) continue;
+      const float2* L = sm + line * P;
+      const float2 zk = L[k == M ? 0 : k];
+      const float2 zc = cconj(L[k == 0 ? 0 : M - k]);
+      const float2 Ev = cscale(cadd(zk, zc), 0.5f);
+      const float2 D = csub(zk, zc);
+      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+      w1[c * cs + (long)row * g.Hx + k] = cadd(Ev, cmul(tw[u], O));
+    }
   }
 }
 
@@ -81,20 +108,32 @@ __global__ void __launch_bounds__(3 * R * S) xi_kernel(const float2* __restrict_
   const int row0 = blockIdx.x * R;
   const int tid = threadIdx.x;
   const long cs = (long)g.nz * g.ny * g.Hx;
-  for (int e = tid; e < 3 * R * M; e += NT) {
-    const int line = e / M, k = e % M;
-    const int r = line / 3, c = line % 3;
-    const int row = row0 + r;
-    float2 z = make_float2(0.f, 0.f);
-    if (row < nrows) {
-      const float2* X = w1 + c * cs + (long)row * g.Hx;
-      const float2 a = __ldg(&X[k]);
-      const float2 b = cconj(__ldg(&X[M - k]));
+  // batches of kB elements per thread: 2 kB independent loads in flight
+  constexpr int kB = 4;
+  for (int e0 = tid; e0 < 3 * R * M; e0 += NT * kB) {
+    float2 A[kB], Bv[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * NT;
+      const int line = e / M, k = e % M;
+      const int r = line / 3, c = line % 3;
+      A[u] = Bv[u] = make_float2(0.f, 0.f);
+      if (e < 3 * R * M && row0 + r < nrows) {
+        const float2* X = w1 + c * cs + (long)(row0 + r) * g.Hx;
+        A[u] = __ldg(&X[k]);
+        Bv[u] = __ldg(&X[M - k]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int e = e0 + u * NT;
+      if (e >= 3 * R * M) break;
+      const int k = e % M;
+      const float2 a = A[u], b = cconj(Bv[u]);
       const float2 Sv = cadd(a, b);
       const float2 t = cmul(cconj(__ldg(&twP[k])), csub(a, b));
-      z = make_float2(Sv.x - t.y, Sv.y + t.x);
+      sm[(e / M) * P + k] = make_float2(Sv.x - t.y, Sv.y + t.x);
     }
-    sm[line * P + k] = z;
   }
   __syncthreads();
   line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
