@@ -340,14 +340,41 @@ def crop_for(name, budget_steps):
     return (side, side, nz)
 
 
+def cpu_model():
+    """Host CPU description from /proc/cpuinfo (x86 'model name', Arm implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    impl = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+    return f"implementer {impl[0]} part {part[0]}" if impl and part else "unknown"
+
+
 def cpu_baseline(name):
+    import torch
     crop = crop_for(name, 2)
     if name == "bulk":
         crop = (256, 256, 16)
     value, secs, threads = time_oracle(name, crop, 2)
+    # the same oracle on one core, on a smaller crop of the same workload
+    crop1 = (64, 64, crop[2]) if name == "bulk" else crop
+    nthreads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        value1, secs1, _ = time_oracle(name, crop1, 2)
+    finally:
+        torch.set_num_threads(nthreads)
     return {"value": value, "unit": "cell-steps/s", "cores": threads, "kind": "oracle",
             "sample": f"2 RK4 steps of the FP64 oracle on a {crop[0]}x{crop[1]}x{crop[2]} crop of the "
-                      f"{name} workload ({secs:.1f} s, torch CPU FFT, {threads} threads)"}
+                      f"{name} workload ({secs:.1f} s, torch CPU FFT, {threads} threads)",
+            "single_core": {"value": value1, "sample": f"2 RK4 steps on a {crop1[0]}x{crop1[1]}x{crop1[2]} crop, "
+                                                       f"1 thread ({secs1:.1f} s)"},
+            "host": {"cpu_count": os.cpu_count(), "cpu_model": cpu_model()}}
 
 
 def run_reference(args, rank, world):
