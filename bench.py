@@ -147,11 +147,11 @@ def workload(name):
     return cfg, m0, Ms, Ku, axis
 
 
-def algorithmic_bytes(cfg, P, ms_map=False, anis_map=False):
+def algorithmic_bytes(cfg, P, ms_map=False, ku_map=False, axis_map=False):
     """Algorithmic HBM bytes per launch of each kernel (FP32 spectra, float4
     fields; a per-cell Ms map adds 4 B/cell to the x pass and the local
-    kernel, an anisotropy map (Ku float + axis float4) 20 B/cell to the local
-    kernel)."""
+    kernel, a Ku map 4 B/cell and an easy-axis map (float4) 16 B/cell to the
+    local kernel)."""
     nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
     Px, Py, Pz = P
     Hx = Px // 2 + 1 if Px > 1 else 1
@@ -159,7 +159,7 @@ def algorithmic_bytes(cfg, P, ms_map=False, anis_map=False):
     w1 = 3 * nz * ny * Hx * 8           # spectrum after the x pass
     w2 = 3 * nz * Py * Hx * 8           # after the y pass
     tensor = (6 if Pz > 1 else 4) * (Pz // 2 + 1) * (Py // 2 + 1) * Hx * 4
-    maps = (4 if ms_map else 0) + (20 if anis_map else 0)
+    maps = (4 if ms_map else 0) + (4 if ku_map else 0) + (16 if axis_map else 0)
     return {
         "x_fwd": nc * (16 + (4 if ms_map else 0)) + w1,
         "y_fwd": w1 + w2,
@@ -250,8 +250,8 @@ def run_mx(args, rank, world, local, name, with_extras=True):
     prof = ctx.profile_step(m, K, dt)
     ctx.sync()
     P = ctx.padded_dims
-    ab = algorithmic_bytes(cfg, P, ms_map=not np.isscalar(Ms),
-                           anis_map=not (np.isscalar(Ku) and np.asarray(axis).ndim <= 1))
+    ab = algorithmic_bytes(cfg, P, ms_map=not np.isscalar(Ms), ku_map=not np.isscalar(Ku),
+                           axis_map=np.asarray(axis).ndim > 1)
     launches = sum(c for (_, c) in prof.values())
     per_step = (launches - 1) / K  # one normalisation per call
     res["launches_per_step"] = per_step

@@ -69,8 +69,7 @@ class Context:
         if isinstance(axis, np.ndarray) and axis.ndim > 1:
             ax_map = to_dev4(axis)
         if ku_map is not None or ax_map is not None:
-            if ku_map is None and ku_scalar != 0.0:
-                ku_map = torch.full(ctx.shape, ku_scalar, dtype=torch.float32, device="cuda")
+            # a scalar Ku stays scalar (the library reads p.Ku where no Ku map is set)
             ctx.set_anis_map(ku_map, ax_map)
         if ctx.params.demag:
             ctx.build_demag_kernel()
