@@ -319,8 +319,65 @@ mx_status mx_cnn_adam_step(mx_cnn *net, double lr, double weight_decay, mx_strea
 
 /* Use `net` (same grid) for the demag term of every later mx_heff,
  * mx_llg_rhs, mx_rk_step and mx_energy call of ctx; NULL returns to the FFT
- * convolution.  The caller keeps `net` alive while it is set. */
+ * convolution.  Setting a net replaces a Fourier neural operator set with
+ * mx_set_demag_fno.  The caller keeps `net` alive while it is set. */
 mx_status mx_set_demag_surrogate(mx_ctx *ctx, mx_cnn *net);
+
+/* ---------------------------------------------------------------------------
+ * Fourier-neural-operator demag surrogate of a film (Sec. II-D: the paper's
+ * network is a 2D FNO with a lifting layer 3 -> 32 channels, four spectral
+ * layers keeping the lowest 12 modes per dimension with complex filters, and
+ * a projection to 3 channels).  Fields are one z plane of ny rows (H) by nx
+ * columns (W):
+ *   v_0 = P x + p;  v_{l+1} = act(K_l v_l + W_l v_l + w_l), act = exact GELU
+ *   for l = 0..2 and the identity for l = 3;  y = Q2 gelu(Q1 v_4 + q1) + q2,
+ *   K_l v = irfft2(R_l . rfft2(v)) on the kept modes ky in [0, K) and
+ *   [H-K, H), kx in [0, K); per mode Y_o = sum_i X_i R_l[mode][i][o].
+ * FP32 throughout.  Normaliser, loss and Adam as for the conv net.
+ * Parameter vector (FP32, DEVICE): P (32x3), p (32), then per layer
+ * R (2K x K x 32 x 32 x 2: mode row with the low corner first, kx, in, out,
+ * re/im), W (32x32, [out][in]), w (32); then Q1 (128x32), q1 (128),
+ * Q2 (3x128), q2 (3).
+ * ------------------------------------------------------------------------- */
+typedef struct mx_fno mx_fno;
+
+/* Number of parameters for K = modes (2,368,259 for K = 12); -1 when modes
+ * is outside 1..16. */
+int mx_fno_num_params(int modes);
+
+/* Network for nx x ny fields (2*modes <= nx, ny <= 1024, 1 <= modes <= 16)
+ * and batches up to max_batch; allocates all of its buffers (about 2.6 kB
+ * per cell of the largest batch).  The parameters start at zero. */
+mx_status mx_fno_create(mx_fno **out, int nx, int ny, int modes, int max_batch);
+mx_status mx_fno_destroy(mx_fno *net);
+
+/* Copy the parameter vector in (resets the Adam moments) / out. */
+mx_status mx_fno_set_params(mx_fno *net, const float *params, mx_stream_t stream);
+mx_status mx_fno_get_params(const mx_fno *net, float *params, mx_stream_t stream);
+
+/* Normaliser, host array: input mean[3], input std[3], output mean[3],
+ * output std[3] (std > 0). */
+mx_status mx_fno_set_normalizer(mx_fno *net, const double stats[12]);
+
+/* h = network(m) for `batch` fields stored back to back (DEVICE float4
+ * arrays of batch*nx*ny records, 16-byte aligned). */
+mx_status mx_fno_forward(mx_fno *net, const float *m, float *h, int batch, mx_stream_t stream);
+
+/* Forward + SmoothL1 loss against h_target (DEVICE float4, raw field) +
+ * backward; the gradient is kept for mx_fno_adam_step, loss_out (DEVICE, 1
+ * float) and grad_out (DEVICE, mx_fno_num_params floats) receive copies
+ * when not NULL. */
+mx_status mx_fno_loss_grad(mx_fno *net, const float *m, const float *h_target, int batch,
+                           float *loss_out, float *grad_out, mx_stream_t stream);
+
+/* One Adam step with the last gradient (as mx_cnn_adam_step). */
+mx_status mx_fno_adam_step(mx_fno *net, double lr, double weight_decay, mx_stream_t stream);
+
+/* Use `net` (same nx, ny; the context must have nz = 1) for the demag term
+ * of every later mx_heff, mx_llg_rhs, mx_rk_step and mx_energy call of ctx;
+ * NULL returns to the FFT convolution.  Replaces a conv net set with
+ * mx_set_demag_surrogate.  The caller keeps `net` alive while it is set. */
+mx_status mx_set_demag_fno(mx_ctx *ctx, mx_fno *net);
 
 /* Relative L2 difference ||a - b|| / ||b|| of two DEVICE float4 fields of
  * the context's grid (xyz only), in FP64; synchronises `stream`. */
@@ -346,7 +403,9 @@ mx_status mx_adjoint_reserve(mx_ctx *ctx, int nsteps, int checkpoint_every);
 /* Forward run for the adjoint: m_final (DEVICE float4) = the field after
  * nsteps RK4 steps of size dt from normalize(m0_raw) (m0_raw DEVICE float4,
  * not modified), keeping the checkpoints the backward run needs.  Direct
- * launches on `stream` (no graph). */
+ * launches on `stream` (no graph).  MX_ERR_UNSUPPORTED while a learned
+ * demag backend is set on a context with demag (the adjoint differentiates
+ * the tensor convolution). */
 mx_status mx_rk_forward_record(mx_ctx *ctx, const float *m0_raw, float *m_final, double dt,
                                mx_stream_t stream);
 

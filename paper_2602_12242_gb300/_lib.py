@@ -77,6 +77,16 @@ SIGNATURES = {
     "mx_cnn_sync": (_I, [_P, _P]),
     "mx_cnn_adam_step": (_I, [_P, _D, _D, _P]),
     "mx_set_demag_surrogate": (_I, [_P, _P]),
+    "mx_fno_num_params": (_I, [_I]),
+    "mx_fno_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
+    "mx_fno_destroy": (_I, [_P]),
+    "mx_fno_set_params": (_I, [_P, _P, _P]),
+    "mx_fno_get_params": (_I, [_P, _P, _P]),
+    "mx_fno_set_normalizer": (_I, [_P, ctypes.POINTER(_D)]),
+    "mx_fno_forward": (_I, [_P, _P, _P, _I, _P]),
+    "mx_fno_loss_grad": (_I, [_P, _P, _P, _I, _P, _P, _P]),
+    "mx_fno_adam_step": (_I, [_P, _D, _D, _P]),
+    "mx_set_demag_fno": (_I, [_P, _P]),
     "mx_rel_l2": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P]),
     "mx_adjoint_reserve": (_I, [_P, _I, _I]),
     "mx_rk_forward_record": (_I, [_P, _P, _P, _D, _P]),
@@ -265,6 +275,50 @@ def mx_cnn_adam_step(net, lr, weight_decay, stream=None):
 
 def mx_set_demag_surrogate(ctx, net):
     check(lib().mx_set_demag_surrogate(ctx, net))
+
+
+def mx_fno_num_params(modes):
+    return int(lib().mx_fno_num_params(int(modes)))
+
+
+def mx_fno_create(nx, ny, modes, max_batch):
+    h = _P()
+    check(lib().mx_fno_create(ctypes.byref(h), int(nx), int(ny), int(modes), int(max_batch)))
+    return h
+
+
+def mx_fno_destroy(net):
+    check(lib().mx_fno_destroy(net))
+
+
+def mx_fno_set_params(net, params, stream=None):
+    check(lib().mx_fno_set_params(net, ptr(params), stream_handle(stream)))
+
+
+def mx_fno_get_params(net, params, stream=None):
+    check(lib().mx_fno_get_params(net, ptr(params), stream_handle(stream)))
+
+
+def mx_fno_set_normalizer(net, stats):
+    arr = (_D * 12)(*[float(v) for v in stats])
+    check(lib().mx_fno_set_normalizer(net, arr))
+
+
+def mx_fno_forward(net, m, h, batch, stream=None):
+    check(lib().mx_fno_forward(net, ptr(m), ptr(h), int(batch), stream_handle(stream)))
+
+
+def mx_fno_loss_grad(net, m, h_target, batch, loss_out=None, grad_out=None, stream=None):
+    check(lib().mx_fno_loss_grad(net, ptr(m), ptr(h_target), int(batch), ptr(loss_out), ptr(grad_out),
+                                 stream_handle(stream)))
+
+
+def mx_fno_adam_step(net, lr, weight_decay, stream=None):
+    check(lib().mx_fno_adam_step(net, float(lr), float(weight_decay), stream_handle(stream)))
+
+
+def mx_set_demag_fno(ctx, net):
+    check(lib().mx_set_demag_fno(ctx, net))
 
 
 def mx_rel_l2(ctx, a, b, stream=None):

@@ -370,7 +370,7 @@ mx_status mx_heff(mx_ctx* ctx, const float* m, float* h, int terms, mx_stream_t 
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool demag = (terms & MX_TERM_DEMAG) != 0;
-  if (demag && !ctx->built && !ctx->surrogate) {
+  if (demag && !ctx->built && !ctx->surrogate && !ctx->fno) {
     set_error("mx_heff: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -389,7 +389,7 @@ mx_status mx_llg_rhs(mx_ctx* ctx, const float* m, float* dmdt, mx_stream_t strea
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool demag = ctx->p.demag != 0;
-  if (demag && !ctx->built && !ctx->surrogate) {
+  if (demag && !ctx->built && !ctx->surrogate && !ctx->fno) {
     set_error("mx_llg_rhs: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -405,7 +405,7 @@ static mx_status check_step_args(mx_ctx* ctx, const float* m, int nsteps, double
     set_error("mx_rk_step: need nsteps >= 0, finite dt > 0, method MX_RK4, MX_EULER or MX_MRI");
     return MX_ERR_INVALID_ARG;
   }
-  if (ctx->p.demag && !ctx->built && !ctx->surrogate) {
+  if (ctx->p.demag && !ctx->built && !ctx->surrogate && !ctx->fno) {
     set_error("mx_rk_step: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -489,7 +489,7 @@ mx_status mx_energy(mx_ctx* ctx, const float* m, double e_out[5], mx_stream_t st
   }
   cudaStream_t st = (cudaStream_t)stream;
   const bool demag = ctx->p.demag != 0;
-  if (demag && !ctx->built && !ctx->surrogate) {
+  if (demag && !ctx->built && !ctx->surrogate && !ctx->fno) {
     set_error("mx_energy: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
@@ -593,6 +593,10 @@ mx_status mx_rk_forward_record(mx_ctx* ctx, const float* m0_raw, float* m_final,
     set_error("mx_rk_forward_record: demag kernel not built");
     return MX_ERR_NOT_BUILT;
   }
+  if (ctx->p.demag && (ctx->surrogate || ctx->fno)) {
+    set_error("mx_rk_forward_record: the adjoint needs the FFT demag (a learned demag backend is set)");
+    return MX_ERR_UNSUPPORTED;
+  }
   return adjoint_forward(ctx, (const float4*)m0_raw, (float4*)m_final, dt, (cudaStream_t)stream);
 }
 
@@ -615,6 +619,19 @@ mx_status mx_set_demag_surrogate(mx_ctx* ctx, mx_cnn* net) {
   }
   invalidate_graph(ctx);
   ctx->surrogate = net;
+  if (net) ctx->fno = nullptr;
+  return MX_OK;
+}
+
+mx_status mx_set_demag_fno(mx_ctx* ctx, mx_fno* net) {
+  MX_TRY(check_ctx(ctx));
+  if (net && !fno_matches(net, ctx->g)) {
+    set_error("mx_set_demag_fno: the network's grid differs from the context's (or nz != 1)");
+    return MX_ERR_INVALID_ARG;
+  }
+  invalidate_graph(ctx);
+  ctx->fno = net;
+  if (net) ctx->surrogate = nullptr;
   return MX_OK;
 }
 

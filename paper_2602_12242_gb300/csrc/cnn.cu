@@ -481,6 +481,15 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+mx_status adam_update(float* p, const float* g, float* m, float* v, long n, double lr, double wd, int t,
+                      cudaStream_t st) {
+  const double b1 = 0.9, b2 = 0.999;
+  const double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+  adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, n, (float)lr, (float)wd, (float)b1,
+                                                           (float)b2, (float)c1, (float)c2, 1e-8f);
+  return launch_check("adam_kernel");
+}
+
 }  // namespace mx
 
 // ---------------------------------------------------------------------------
@@ -830,13 +839,7 @@ mx_status mx_cnn_adam_step(mx_cnn* n, double lr, double weight_decay, mx_stream_
   }
   cudaStream_t st = (cudaStream_t)stream;
   n->adam_t += 1;
-  const double b1 = 0.9, b2 = 0.999;
-  const double c1 = 1.0 - pow(b1, n->adam_t), c2 = 1.0 - pow(b2, n->adam_t);
-  const long np = num_params_total();
-  adam_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(n->params, n->grad, n->am, n->av, np, (float)lr,
-                                                            (float)weight_decay, (float)b1, (float)b2, (float)c1,
-                                                            (float)c2, 1e-8f);
-  MX_TRY(launch_check("adam_kernel"));
+  MX_TRY(adam_update(n->params, n->grad, n->am, n->av, num_params_total(), lr, weight_decay, n->adam_t, st));
   return pack_all(n, st);
 }
 

@@ -167,8 +167,10 @@ struct mx_ctx {
   // adjoint workspaces (mx_adjoint_reserve)
   mx::AdjWork* adj = nullptr;
 
-  // learned demag backend (mx_set_demag_surrogate); NULL: FFT convolution
+  // learned demag backend (mx_set_demag_surrogate / mx_set_demag_fno; at
+  // most one is set); both NULL: FFT convolution
   struct mx_cnn* surrogate = nullptr;
+  struct mx_fno* fno = nullptr;
   float4* mri_f = nullptr;        // MRI slow right-hand sides F_1..F_3 (allocated at first use)
   double* red2 = nullptr;         // 2 FP64 accumulators for mx_rel_l2
 };

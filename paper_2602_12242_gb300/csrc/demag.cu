@@ -318,6 +318,7 @@ mx_status demag_setup(mx_ctx* ctx) {
 
 mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st) {
   if (ctx->surrogate) return cnn_demag(ctx->surrogate, m, hd, st);
+  if (ctx->fno) return fno_demag(ctx->fno, m, hd, st);
   if (ctx->plane) return plane_field(ctx, m, hd, st);
   const Grid& g = ctx->g;
   const int rows = x_rows(g);

@@ -50,6 +50,13 @@ mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 // cnn.cu
 mx_status cnn_demag(struct mx_cnn* n, const float4* m, float4* h, cudaStream_t st);
 bool cnn_matches(const struct mx_cnn* n, const Grid& g);
+// Adam with L2-coupled weight decay (beta 0.9 / 0.999, eps 1e-8), step t >= 1.
+mx_status adam_update(float* p, const float* g, float* m, float* v, long n, double lr, double wd, int t,
+                      cudaStream_t st);
+
+// fno.cu
+mx_status fno_demag(struct ::mx_fno* n, const float4* m, float4* h, cudaStream_t st);
+bool fno_matches(const struct ::mx_fno* n, const Grid& g);
 
 // dftgemm.cu
 mx_status dft_gemm_setup(mx_ctx* ctx);

@@ -1,8 +1,9 @@
 """Learned demag surrogate: network handle, dataset, training loop and the
 in-loop driver with the FFT demag as judge and fallback.
 
-All arithmetic of the network (forward, loss, backward, Adam) and of the
-micromagnetic path runs in libmx (mx_cnn_*, mx_heff, mx_rk_step, mx_rel_l2);
+All arithmetic of the networks (forward, loss, backward, Adam) and of the
+micromagnetic path runs in libmx (mx_cnn_*, mx_fno_*, mx_heff, mx_rk_step,
+mx_rel_l2);
 this module only moves tensors, draws seeded inputs and runs the control flow
 of training (batching, learning-rate schedule) and of the judge.
 """
@@ -84,6 +85,102 @@ class Surrogate:
     def adam_step(self, lr, weight_decay):
         L.mx_cnn_adam_step(self.h, lr, weight_decay)
 
+    def forward_into(self, m, h, batch):
+        L.mx_cnn_forward(self.h, m, h, batch)
+
+    def attach(self, ctx_h):
+        """Make this net the demag backend of a context (None: detach)."""
+        L.mx_set_demag_surrogate(ctx_h, self.h)
+
+    @staticmethod
+    def detach(ctx_h):
+        L.mx_set_demag_surrogate(ctx_h, None)
+
+
+def init_fno_params(modes, seed):
+    """Seeded initial parameters of the Fourier neural operator, in the
+    library's order: pointwise weights and biases uniform in +-1/sqrt(fan_in),
+    spectral filters (real and imaginary parts) uniform in [0, 1/(32*32))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+
+    def lin(cout, cin):
+        bound = 1.0 / np.sqrt(cin)
+        parts.append(rng.uniform(-bound, bound, size=cout * cin))
+        parts.append(rng.uniform(-bound, bound, size=cout))
+
+    lin(32, 3)
+    for _ in range(4):
+        parts.append(rng.uniform(0.0, 1.0 / (32 * 32), size=2 * modes * modes * 32 * 32 * 2))
+        lin(32, 32)
+    lin(128, 32)
+    lin(3, 128)
+    return np.concatenate(parts).astype(np.float32)
+
+
+class FourierSurrogate:
+    """The 2D Fourier neural operator of libmx for one film grid (nz = 1)."""
+
+    def __init__(self, nx, ny, modes=12, max_batch=1):
+        self.shape = (1, int(ny), int(nx))
+        self.modes = int(modes)
+        self.max_batch = int(max_batch)
+        self.h = None
+        self.h = L.mx_fno_create(nx, ny, modes, max_batch)
+        self.n_params = L.mx_fno_num_params(modes)
+
+    def close(self):
+        if self.h is not None:
+            L.mx_fno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        flat = torch.as_tensor(flat, dtype=torch.float32, device="cuda").contiguous()
+        assert flat.numel() == self.n_params
+        L.mx_fno_set_params(self.h, flat)
+
+    def get_params(self):
+        out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        L.mx_fno_get_params(self.h, out)
+        torch.cuda.current_stream().synchronize()
+        return out
+
+    def set_normalizer(self, stats):
+        self.stats = [float(v) for v in stats]
+        L.mx_fno_set_normalizer(self.h, self.stats)
+
+    def forward(self, m):
+        b = m.shape[0] if m.dim() == 5 else 1
+        h = torch.empty_like(m)
+        L.mx_fno_forward(self.h, m.contiguous(), h, b)
+        return h
+
+    def forward_into(self, m, h, batch):
+        L.mx_fno_forward(self.h, m, h, batch)
+
+    def loss_grad(self, m, h_target, want_grad=True):
+        b = m.shape[0] if m.dim() == 5 else 1
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        grad = torch.empty(self.n_params, dtype=torch.float32, device="cuda") if want_grad else None
+        L.mx_fno_loss_grad(self.h, m.contiguous(), h_target.contiguous(), b, loss, grad)
+        return loss, grad
+
+    def adam_step(self, lr, weight_decay):
+        L.mx_fno_adam_step(self.h, lr, weight_decay)
+
+    def attach(self, ctx_h):
+        L.mx_set_demag_fno(ctx_h, self.h)
+
+    @staticmethod
+    def detach(ctx_h):
+        L.mx_set_demag_fno(ctx_h, None)
+
 
 def make_dataset(ctx, n, seed0=5000, sigma=8.0, chunk=256):
     """n seeded smooth-noise textures (normalised) and their FFT demag fields.
@@ -139,7 +236,7 @@ def run_in_loop(ctx, net, m, nsteps, dt, judge_every, threshold=1e-2):
     errors, fallback = [], None
     hs = torch.empty_like(m)
     hf = torch.empty_like(m)
-    L.mx_set_demag_surrogate(ctx.h, net.h)
+    net.attach(ctx.h)
     try:
         done = 0
         while done < nsteps:
@@ -148,16 +245,16 @@ def run_in_loop(ctx, net, m, nsteps, dt, judge_every, threshold=1e-2):
             done += k
             if fallback is None:
                 ctx.heff(m, out=hs, terms=L.MX_TERM_DEMAG)
-                L.mx_set_demag_surrogate(ctx.h, None)
+                net.detach(ctx.h)
                 ctx.heff(m, out=hf, terms=L.MX_TERM_DEMAG)
                 err = L.mx_rel_l2(ctx.h, hs, hf)
                 errors.append((done, err))
                 if err > threshold:
                     fallback = done
                 else:
-                    L.mx_set_demag_surrogate(ctx.h, net.h)
+                    net.attach(ctx.h)
     finally:
-        L.mx_set_demag_surrogate(ctx.h, None)
+        net.detach(ctx.h)
     ctx.sync()
     return {"errors": errors, "fallback_step": fallback}
 
@@ -175,7 +272,7 @@ def time_batched(ctx, net, M, reps=10):
                 for i in range(b):
                     ctx.heff(M[i], out=h[i], terms=L.MX_TERM_DEMAG)
             else:
-                L.mx_cnn_forward(net.h, M[:b].contiguous(), h, b)
+                net.forward_into(M[:b].contiguous(), h, b)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -184,7 +281,7 @@ def time_batched(ctx, net, M, reps=10):
                 for i in range(b):
                     ctx.heff(M[i], out=h[i], terms=L.MX_TERM_DEMAG)
             else:
-                L.mx_cnn_forward(net.h, M[:b].contiguous(), h, b)
+                net.forward_into(M[:b].contiguous(), h, b)
         e1.record()
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / (reps * b)
@@ -196,8 +293,11 @@ def time_demag(ctx, net, m, reps=50):
     """Mean time [ms] of one demag evaluation by the FFT convolution and by the surrogate."""
     h = torch.empty_like(m)
     out = {}
-    for name, backend in (("fft", None), ("surrogate", net.h)):
-        L.mx_set_demag_surrogate(ctx.h, backend)
+    for name in ("fft", "surrogate"):
+        if name == "fft":
+            net.detach(ctx.h)
+        else:
+            net.attach(ctx.h)
         for _ in range(3):
             ctx.heff(m, out=h, terms=L.MX_TERM_DEMAG)
         torch.cuda.synchronize()
@@ -209,5 +309,5 @@ def time_demag(ctx, net, m, reps=50):
         e1.record()
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / reps
-    L.mx_set_demag_surrogate(ctx.h, None)
+    net.detach(ctx.h)
     return out
