@@ -227,7 +227,8 @@ __global__ void __launch_bounds__(256) fno_idft_x_kernel(const float2* __restric
 }
 
 // Projection q = Q2 gelu(Q1 v + q1) + q2 per cell (one thread per cell).
-// INFER: h = q * std + mean (float4); else pred = q, and z1 (pre-GELU hidden) is stored.
+// INFER: h = q * std + mean (float4); else pred = q, and z1 (pre-GELU hidden)
+// is stored hidden-major, z1[j * ncells + cell], so a warp's stores coalesce.
 template <bool INFER>
 __global__ void __launch_bounds__(128) fno_proj_kernel(const float* __restrict__ v, long ncells,
                                                        const float* __restrict__ Q1, const float* __restrict__ q1,
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(128) fno_proj_kernel(const float* __restrict__
     float z = sq1[j];
 #pragma unroll
     for (int i = 0; i < kFC; ++i) z = fmaf(sQ1[j][i], a[i], z);
-    if (!INFER) z1[cell * kFH + j] = z;
+    if (!INFER) z1[(long)j * ncells + cell] = z;
     const float h = fgelu(z);
     o0 = fmaf(sQ2[0][j], h, o0);
     o1 = fmaf(sQ2[1][j], h, o1);
@@ -295,6 +296,7 @@ __global__ void fno_loss_kernel(const float4* __restrict__ pred, const float4* _
 
 // Projection backward per cell: dz1[j] = gelu'(z1[j]) sum_k Q2[k][j] g[k];
 // dv[i] = sum_j Q1[j][i] dz1[j] (the last spectral layer has no activation).
+// z1 and dz1 are hidden-major ([j][cell]).
 __global__ void __launch_bounds__(128) fno_proj_bwd_kernel(const float4* __restrict__ g, const float* __restrict__ z1,
                                                            long ncells, const float* __restrict__ Q1,
                                                            const float* __restrict__ Q2, float* __restrict__ dz1,
@@ -311,9 +313,9 @@ __global__ void __launch_bounds__(128) fno_proj_bwd_kernel(const float4* __restr
 #pragma unroll
   for (int i = 0; i < kFC; ++i) d[i] = 0.f;
   for (int j = 0; j < kFH; ++j) {
-    const float z = z1[cell * kFH + j];
+    const float z = z1[(long)j * ncells + cell];
     const float dz = fgelu_grad(z) * (sQ2[0][j] * gc.x + sQ2[1][j] * gc.y + sQ2[2][j] * gc.z);
-    dz1[cell * kFH + j] = dz;
+    dz1[(long)j * ncells + cell] = dz;
 #pragma unroll
     for (int i = 0; i < kFC; ++i) d[i] = fmaf(sQ1[j][i], dz, d[i]);
   }
@@ -324,8 +326,10 @@ __global__ void __launch_bounds__(128) fno_proj_bwd_kernel(const float4* __restr
 
 // Pointwise weight gradient over cells: dW[m][n] += sum_c A[c][m] f(Bv[c][n]),
 // db[m] += sum_c A[c][m]; f = gelu when gelu_b.  A has M used columns of row
-// stride lda, Bv N of stride ldb.  Each block sums a chunk of cells, then adds
-// its partial sums with FP32 atomics.
+// stride lda; Bv has N columns of row stride ldb, or (ldb = 0) is stored
+// column-major, Bv[n * ncells + c].  Each block sums a chunk of cells, then adds
+// its partial sums with FP32 atomics (the general form; the 128 x 32 and
+// 32 x 32 cases take the register-tiled kernel below).
 constexpr int kWgTile = 32;
 __global__ void __launch_bounds__(256) fno_wgrad_kernel(const float* __restrict__ Av, int M, int lda,
                                                         const float* __restrict__ Bv, int N, int ldb, int gelu_b,
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(256) fno_wgrad_kernel(const float* __restrict_
         if (nn == N) {
           b = 1.f;
         } else {
-          b = Bv[(t0 + c) * ldb + nn];
+          b = ldb ? Bv[(t0 + c) * ldb + nn] : Bv[(long)nn * ncells + t0 + c];
           if (gelu_b) b = fgelu(b);
         }
       }
@@ -384,6 +388,71 @@ __global__ void __launch_bounds__(256) fno_wgrad_kernel(const float* __restrict_
       else
         atomicAdd(&dW[mm * N + nn], acc[k]);
     }
+  }
+}
+
+// The same sum for M = 128 or 32 rows and N = 32 columns (B with row stride
+// N; A with row stride M, or column-major A[m * ncells + c] when A_CM), as a
+// register-tiled product: thread (tm, tn) owns rows tm*TM.. and columns
+// tn*TN.. and reads TM + TN values per cell for TM*TN FMAs.
+template <int M, int N, int TM, int TN, bool A_CM>
+__global__ void __launch_bounds__(256) fno_wgrad_tiled_kernel(const float* __restrict__ Av,
+                                                              const float* __restrict__ Bv, long ncells, long chunk,
+                                                              float* __restrict__ dW, float* __restrict__ db) {
+  static_assert((M / TM) * (N / TN) == 256, "one output tile per thread");
+  __shared__ __align__(16) float As[kWgTile][M];
+  __shared__ __align__(16) float Bs[kWgTile][N];
+  const int tm = threadIdx.x % (M / TM), tn = threadIdx.x / (M / TM);
+  const int m0 = tm * TM, n0 = tn * TN;
+  float acc[TM][TN], bacc[TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    bacc[a] = 0.f;
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = 0.f;
+  }
+  const long c0 = (long)blockIdx.x * chunk;
+  const long c1 = min(ncells, c0 + chunk);
+  for (long t0 = c0; t0 < c1; t0 += kWgTile) {
+    const int nt = (int)min((long)kWgTile, c1 - t0);
+    __syncthreads();
+    if (A_CM) {
+      // lanes take consecutive cells of one row m (coalesced reads)
+      for (int q = threadIdx.x; q < kWgTile * M; q += 256) {
+        const int c = q % kWgTile, mm = q / kWgTile;
+        As[c][mm] = c < nt ? Av[(long)mm * ncells + t0 + c] : 0.f;
+      }
+    } else {
+      for (int q = threadIdx.x; q < kWgTile * M / 4; q += 256) {
+        const int c = q / (M / 4);
+        ((float4*)&As[0][0])[q] = c < nt ? ((const float4*)(Av + t0 * M))[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    for (int q = threadIdx.x; q < kWgTile * N / 4; q += 256) {
+      const int c = q / (N / 4);
+      ((float4*)&Bs[0][0])[q] = c < nt ? ((const float4*)(Bv + t0 * N))[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < kWgTile; ++c) {
+      float a[TM], b[TN];
+#pragma unroll
+      for (int q = 0; q < TM; ++q) a[q] = As[c][m0 + q];
+#pragma unroll
+      for (int q = 0; q < TN; ++q) b[q] = Bs[c][n0 + q];
+#pragma unroll
+      for (int x = 0; x < TM; ++x) {
+        bacc[x] += a[x];
+#pragma unroll
+        for (int y = 0; y < TN; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+      }
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < TM; ++x) {
+#pragma unroll
+    for (int y = 0; y < TN; ++y) atomicAdd(&dW[(m0 + x) * N + n0 + y], acc[x][y]);
+    if (tn == 0) atomicAdd(&db[m0 + x], bacc[x]);
   }
 }
 
@@ -533,9 +602,23 @@ static mx_status fno_forward(mx_fno* n, const float4* m, int B, bool train, floa
 
 static mx_status fno_wgrad(const float* A, int M, int lda, const float* Bv, int N, int ldb, bool gelu_b, long nc,
                            float* dW, float* db, cudaStream_t st) {
-  long chunk = 1024;
-  while (chunk > kWgTile && (nc + chunk - 1) / chunk < 2 * 152) chunk /= 2;
+  // about two blocks per SM, each summing a whole number of 32-cell tiles
+  long chunk = (nc + 2 * 152 - 1) / (2 * 152);
+  chunk = ((chunk + kWgTile - 1) / kWgTile) * kWgTile;
   const unsigned grid = (unsigned)((nc + chunk - 1) / chunk);
+  // lda = 0: A column-major (A[m * nc + c]); ldb = 0: B column-major
+  if (!gelu_b && ldb == N && N == kFC && M == kFH && lda == 0) {
+    fno_wgrad_tiled_kernel<kFH, kFC, 4, 4, true><<<grid, 256, 0, st>>>(A, Bv, nc, chunk, dW, db);
+    return launch_check("fno_wgrad_tiled_kernel");
+  }
+  if (!gelu_b && ldb == N && N == kFC && M == kFC && lda == M) {
+    fno_wgrad_tiled_kernel<kFC, kFC, 2, 2, false><<<grid, 256, 0, st>>>(A, Bv, nc, chunk, dW, db);
+    return launch_check("fno_wgrad_tiled_kernel");
+  }
+  if (lda == 0) {
+    set_error("fno_wgrad: column-major A is only supported for the 128 x 32 case");
+    return MX_ERR_INVALID_ARG;
+  }
   const size_t sm = (size_t)kWgTile * (M + N + 1) * sizeof(float);
   fno_wgrad_kernel<<<grid, 256, sm, st>>>(A, M, lda, Bv, N, ldb, gelu_b ? 1 : 0, nc, chunk, dW, db);
   return launch_check("fno_wgrad_kernel");
@@ -552,8 +635,8 @@ static mx_status fno_backward(mx_fno* n, int B, cudaStream_t st) {
   // projection: dz1, dv4 (= dL/du_3), then dQ1/dq1 and dQ2/dq2
   fno_proj_bwd_kernel<<<pg, 128, 0, st>>>(n->g, n->z1, nc, P + f.Q1, P + f.Q2, n->dz1, n->du[0]);
   MX_TRY(launch_check("fno_proj_bwd_kernel"));
-  MX_TRY(fno_wgrad(n->dz1, kFH, kFH, n->v[kFL], kFC, kFC, false, nc, G + f.Q1, G + f.q1, st));
-  MX_TRY(fno_wgrad((const float*)n->g, 3, 4, n->z1, kFH, kFH, true, nc, G + f.Q2, G + f.q2, st));
+  MX_TRY(fno_wgrad(n->dz1, kFH, 0, n->v[kFL], kFC, kFC, false, nc, G + f.Q1, G + f.q1, st));
+  MX_TRY(fno_wgrad((const float*)n->g, 3, 4, n->z1, kFH, 0, true, nc, G + f.Q2, G + f.q2, st));
   int cur = 0;
   for (int l = kFL - 1; l >= 0; --l) {
     const float* du = n->du[cur];

@@ -21,6 +21,19 @@ trajectory: snapshots of m every --every RK4 steps of a workload from its
 fft-mode timing: per-kernel time of the bulk RK4 step with FP32 x transforms
   and with the split-BF16 DFT-as-GEMM first x stage.
 
+  python -m paper_2602_12242_gb300.patterns --fno [--train-sims N] [--frames F] [--epochs E] [--batch B] [--out FILE]
+
+fno: the Fourier-neural-operator surrogate and the conv net trained on the
+  same SP4 film pairs (160x40x1 cells of 3.125 nm; S-state, then random
+  in-plane fields of 25-40 mT, F snapshots over 1 ns each); held-out demag
+  error, <m>(t) over 1 ns under the two SP4 fields with each network as the
+  demag backend against the FFT run, and times.
+
+  python -m paper_2602_12242_gb300.patterns --fno-timing
+
+fno timing: per-call time of FNO inference (1 field, 128 fields) and of one
+  training step of 128 fields on the SP4 film grid.
+
   python -m paper_2602_12242_gb300.patterns --mri
 
 mri: time to solution of RK4 and of the explicit-explicit MRI step on the SP4
@@ -37,8 +50,8 @@ import torch
 from . import _lib as L
 from . import inputs
 from .solver import Context, to_dev4
-from .surrogate import (Surrogate, init_params, make_dataset, normalizer_stats, run_in_loop, time_batched, time_demag,
-                        train)
+from .surrogate import (FourierSurrogate, Surrogate, init_fno_params, init_params, make_dataset, normalizer_stats,
+                        run_in_loop, time_batched, time_demag, train)
 
 
 def _rk_time(ctx, m, n, dt):
@@ -105,6 +118,165 @@ def learned_report(pairs, epochs, batch, insteps, judge, holdout=64, log=print):
                     "free_run_errors": res_free["errors"][:: max(1, len(res_free["errors"]) // 10)],
                     "max_drift_m_free_run": drift_free, "max_drift_m_judged_run": drift_judged},
     }
+
+
+SP4_FILM = dict(nx=160, ny=40, nz=1, dx=3.125e-9, dy=3.125e-9, dz=3.125e-9, Ms=8e5, A=1.3e-11, Ku=0.0,
+                ku_axis=(0.0, 0.0, 1.0), D=0.0, dmi=False, alpha=0.02, gamma=2.211e5, h_bias=(0.0, 0.0, 0.0))
+MU0 = 4e-7 * np.pi
+
+
+def sp4_s_state(dt=1e-13):
+    """The S-state of Sec. III-D: m = (1, 0, 0), alpha 0.5, a (1e5, 1e5, 1e5) A/m
+    field for 20 ps, ramped linearly to zero over 10 ps (in 1 ps steps), then
+    1 ns of relaxation without field (RK4)."""
+    cfg = dict(SP4_FILM, alpha=0.5)
+    ctx = Context.from_config(cfg)
+    m0 = np.zeros((1, cfg["ny"], cfg["nx"], 3))
+    m0[..., 0] = 1.0
+    m = to_dev4(m0)
+    ctx.set_bias((1e5, 1e5, 1e5))
+    ctx.rk_step(m, int(round(20e-12 / dt)), dt)
+    for q in range(10):
+        f = 1e5 * (1.0 - (q + 0.5) / 10.0)
+        ctx.set_bias((f, f, f))
+        ctx.rk_step(m, int(round(1e-12 / dt)), dt)
+    ctx.set_bias((0.0, 0.0, 0.0))
+    ctx.rk_step(m, int(round(1e-9 / dt)), dt)
+    ctx.sync()
+    ctx.close()
+    return m
+
+
+def sp4_fields(n, seed):
+    """n bias fields of Sec. II-D: magnitude uniform in 25-40 mT, direction
+    uniform on the sphere projected into the film plane [A/m]."""
+    r = inputs.rng(seed)
+    v = r.normal(size=(n, 3))
+    v[:, 2] = 0.0
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    mag = r.uniform(25e-3, 40e-3, size=n) / MU0
+    return v * mag[:, None]
+
+
+def sp4_dataset(ctx, s_state, fields, T=1e-9, frames=20, dt=1e-13):
+    """(m, H_demag) pairs: from the S-state, each field drives the film for T
+    (RK4, alpha 0.02); a snapshot every T/frames."""
+    n = len(fields) * frames
+    M = torch.empty((n,) + tuple(s_state.shape), dtype=torch.float32, device="cuda")
+    H = torch.empty_like(M)
+    every = int(round(T / frames / dt))
+    q = 0
+    for f in fields:
+        ctx.set_bias(tuple(float(v) for v in f))
+        m = s_state.clone()
+        for _ in range(frames):
+            ctx.rk_step(m, every, dt)
+            M[q] = m
+            ctx.heff(m, out=H[q], terms=L.MX_TERM_DEMAG)
+            q += 1
+    torch.cuda.synchronize()
+    return M, H
+
+
+def mean_m_curve(ctx, m, steps, every, dt, net=None):
+    """<m> every `every` RK4 steps (the net, if given, as the demag backend)."""
+    out = []
+    if net is not None:
+        net.attach(ctx.h)
+    try:
+        for _ in range(steps // every):
+            ctx.rk_step(m, every, dt)
+            out.append(m[..., :3].double().mean(dim=(0, 1, 2)))
+    finally:
+        if net is not None:
+            net.detach(ctx.h)
+    ctx.sync()
+    return torch.stack(out).cpu().numpy()
+
+
+def fno_report(train_sims=96, val_sims=8, frames=100, epochs=100, batch=32, modes=12, log=print):
+    """The FNO surrogate (Sec. II-D) and the conv net trained on the same SP4
+    film pairs (160 x 40 x 1, 3.125 nm): held-out demag error, in-loop <m>(t)
+    under the two SP4 fields against the FFT run, and times."""
+    dt = 1e-13
+    t0 = time.perf_counter()
+    s_state = sp4_s_state(dt)
+    ctx = Context.from_config(dict(SP4_FILM))
+    fields = sp4_fields(train_sims + val_sims, 2602)
+    M, H = sp4_dataset(ctx, s_state, fields, frames=frames, dt=dt)
+    t_data = time.perf_counter() - t0
+    ntr = train_sims * frames
+    stats = normalizer_stats(M[:ntr], H[:ntr])
+    nets = {
+        "fno": FourierSurrogate(SP4_FILM["nx"], SP4_FILM["ny"], modes, max_batch=batch),
+        "cnn": Surrogate(SP4_FILM["nx"], SP4_FILM["ny"], 1, max_batch=batch),
+    }
+    nets["fno"].set_params(torch.as_tensor(init_fno_params(modes, 12)))
+    nets["cnn"].set_params(torch.as_tensor(init_params(11)))
+    out = {"workload": "SP4 film 160x40x1 (3.125 nm), S-state + random in-plane fields 25-40 mT",
+           "train_pairs": ntr, "val_pairs": val_sims * frames, "epochs": epochs, "batch": batch, "modes": modes,
+           "dataset_s": t_data, "params": {k: n.n_params for k, n in nets.items()}}
+    ms = (20, 40, 60)
+    sp4 = {"field1": (-19576.0, 3422.0, 0.0), "field2": (-28259.0, -5013.0, 0.0)}
+    curves = {}
+    for f, hb in sp4.items():
+        ctx.set_bias(hb)
+        curves[(f, "fft")] = mean_m_curve(ctx, s_state.clone(), 10000, 100, dt)
+    for name, net in nets.items():
+        net.set_normalizer(stats)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        losses = train(net, M[:ntr], H[:ntr], epochs=epochs, batch=batch, milestones=ms, log=None)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t1
+        errs = [L.mx_rel_l2(ctx.h, net.forward(M[i]), H[i]) for i in range(ntr, M.shape[0])]
+        r = {"train_s": t_train, "train_samples_per_s": ntr * epochs / t_train,
+             "loss_first_last": [losses[0], losses[-1]],
+             "val_rel_l2_mean": float(np.mean(errs)), "val_rel_l2_max": float(np.max(errs)),
+             "demag_eval_ms": time_demag(ctx, net, M[ntr].clone()),
+             "batched_demag_ms_per_field": time_batched(ctx, net, M[ntr:ntr + batch])}
+        for f, hb in sp4.items():
+            ctx.set_bias(hb)
+            c = mean_m_curve(ctx, s_state.clone(), 10000, 100, dt, net)
+            ref = curves[(f, "fft")]
+            r[f] = {"max_abs_mean_m_err": [float(v) for v in np.abs(c - ref).max(axis=0)],
+                    "mean_m_at_1ns": [float(v) for v in c[-1]], "fft_mean_m_at_1ns": [float(v) for v in ref[-1]]}
+        out[name] = r
+        if log:
+            log(f"{name}: {json.dumps(r)}")
+    return out
+
+
+def fno_timing(batch=128, modes=12, reps=20):
+    """Per-call times of the FNO on the SP4 film grid with seeded parameters
+    and fields: inference of one field, inference of `batch` fields, and one
+    training step (loss, gradient and Adam) of `batch` fields."""
+    nx, ny = SP4_FILM["nx"], SP4_FILM["ny"]
+    net = FourierSurrogate(nx, ny, modes, max_batch=batch)
+    net.set_params(torch.as_tensor(init_fno_params(modes, 12)))
+    net.set_normalizer([0.0, 0.0, 0.0, 0.5, 0.5, 0.5, 0.0, 0.0, 0.0, 1e5, 1e5, 1e5])
+    M = torch.stack([to_dev4(inputs.smooth_texture((1, ny, nx), 8.0, 7000 + i)) for i in range(batch)])
+    Ht = torch.empty_like(M)
+    h1 = torch.empty_like(M[:1])
+    out = {"grid": f"{nx}x{ny}x1", "modes": modes, "batch": batch}
+    runs = {"infer_1": lambda: net.forward_into(M[:1], h1, 1),
+            "infer_batch": lambda: net.forward_into(M, Ht, batch),
+            "train_step_batch": lambda: (net.loss_grad(M, Ht, want_grad=False), net.adam_step(1e-4, 1e-4))}
+    for name, fn in runs.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    out["infer_ms_per_field_batch"] = out["infer_batch_ms"] / batch
+    out["train_samples_per_s"] = batch / (out["train_step_batch_ms"] * 1e-3)
+    net.close()
+    return out
 
 
 def adjoint_report(nsteps=2000, every=100):
@@ -219,6 +391,10 @@ def main():
     ap.add_argument("--perturb", action="store_true")
     ap.add_argument("--fft-mode-timing", action="store_true")
     ap.add_argument("--mri", action="store_true")
+    ap.add_argument("--fno", action="store_true")
+    ap.add_argument("--fno-timing", action="store_true")
+    ap.add_argument("--train-sims", type=int, default=96)
+    ap.add_argument("--frames", type=int, default=100)
     ap.add_argument("--pairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--batch", type=int, default=128)
@@ -229,6 +405,16 @@ def main():
     a = ap.parse_args()
     if a.mri:
         print(json.dumps(mri_report()), flush=True)
+        return
+    if a.fno_timing:
+        print(json.dumps(fno_timing()), flush=True)
+        return
+    if a.fno:
+        s = json.dumps(fno_report(train_sims=a.train_sims, frames=a.frames, epochs=a.epochs, batch=a.batch))
+        print(s, flush=True)
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(s + "\n")
         return
     if a.fft_mode_timing:
         print(json.dumps(fft_mode_timing()), flush=True)
