@@ -163,3 +163,28 @@ def test_film_demag_backend_and_refusals():
     with pytest.raises(MxError):
         FourierSurrogate(64, 64, 17, 1)  # K > 16
     assert _lib.mx_fno_num_params(12) == fno.num_params(12)
+
+
+def test_training_reduces_loss_and_in_loop_fallback():
+    """Training through the C ABI lowers the loss; as the demag backend of a
+    film run the FFT judge (threshold 1e-2) rejects the briefly trained
+    network at its first check, and a loose threshold leaves it in charge."""
+    from helpers import cfg_of, context
+    from paper_2602_12242_gb300.surrogate import (FourierSurrogate, init_fno_params, make_dataset, normalizer_stats,
+                                                  run_in_loop, train)
+    c = cfg_of(nx=48, ny=32, nz=1, dx=3.125e-9, dy=3.125e-9, dz=3.125e-9)
+    ctx = context(c)
+    M, H = make_dataset(ctx, 96, seed0=9100)
+    net = FourierSurrogate(48, 32, 6, max_batch=16)
+    net.set_params(torch.as_tensor(init_fno_params(6, 3)))
+    net.set_normalizer(normalizer_stats(M, H))
+    losses = train(net, M, H, epochs=10, batch=16, lr=2e-3)
+    assert losses[-1] < 0.7 * losses[0], losses
+    m = M[0].clone()
+    res = run_in_loop(ctx, net, m, nsteps=6, dt=1e-14, judge_every=3, threshold=1e-2)
+    assert res["errors"] and res["fallback_step"] == 3
+    nrm = torch.linalg.vector_norm(m[..., :3], dim=-1)
+    assert float((nrm - 1).abs().max()) < 1e-5
+    m2 = M[1].clone()
+    res2 = run_in_loop(ctx, net, m2, nsteps=6, dt=1e-14, judge_every=3, threshold=10.0)
+    assert res2["fallback_step"] is None and len(res2["errors"]) == 2
