@@ -1,0 +1,39 @@
+"""Host arithmetic of bench.py's roofline object (CPU only)."""
+import json
+import os
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_algorithmic_bytes_of_the_bulk_step():
+    """Bulk grid 512 x 512 x 16 (padded 1024 x 1024 x 32): the x-pass spectrum
+    holds 3 components x 16 planes x 512 rows x 513 complex FP32; the tensor
+    octant 6 components x 17 x 513 x 513 FP32; fields are 16-byte float4."""
+    cfg = dict(nx=512, ny=512, nz=16)
+    b = bench.algorithmic_bytes(cfg, (1024, 1024, 32))
+    cells = 512 * 512 * 16
+    w1 = 3 * 16 * 512 * 513 * 8
+    octant = 6 * 17 * 513 * 513 * 4
+    assert w1 == 100_859_904 and octant == 107_372_952
+    assert b["yz_fused"] == 2 * w1 + octant == 309_092_760
+    assert b["x_fwd"] == b["x_inv"] == cells * 16 + w1
+    # RK4 stages read/write 64, 96, 96 and 80 bytes per cell (no maps)
+    assert b["local_stage"] == cells * 84
+    assert bench.algorithmic_bytes(cfg, (1024, 1024, 32), axis_map=True)["local_stage"] == cells * 100
+
+
+def test_film_spectrum_has_four_tensor_components():
+    """One z plane: N_xz = N_yz = 0, so the octant keeps four components."""
+    b = bench.algorithmic_bytes(dict(nx=512, ny=128, nz=1), (1024, 256, 1))
+    assert b["yz_fused"] == 2 * (3 * 128 * 513 * 8) + 4 * 1 * 129 * 513 * 4
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    entry = t["bulk"]["yz_fused"]
+    monkeypatch.setattr(bench, "source_digest", lambda: entry["source_digest"])
+    assert bench.load_traffic("bulk", "yz_fused") == entry["dram_bytes_per_launch"]
+    monkeypatch.setattr(bench, "source_digest", lambda: "0" * 16)
+    assert bench.load_traffic("bulk", "yz_fused") is None
