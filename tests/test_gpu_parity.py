@@ -181,6 +181,25 @@ def test_short_trajectory_matches_oracle(method):
     assert np.abs(np.linalg.norm(got, axis=-1) - 1).max() <= 1e-6
 
 
+@pytest.mark.parametrize("method", ["rk4", "euler"])
+def test_relaxation_without_precession_matches_oracle(method):
+    """The precession switch (damping term only, for relaxation to a state):
+    dm/dt and a short run against the oracle with the same switch, DMI and
+    chiral edges included."""
+    c = CASES["ragged37x21x5"]
+    m0 = f32(random_m(c, 17))
+    ctx = context(c, precession=False)
+    p = problem(c, precession=False)
+    k = host(ctx.llg_rhs(gpu_m(m0)))
+    kref = mm.llg_rhs(p, t64(m0), mm.heff(p, t64(m0))).numpy()
+    assert rel_l2(k, kref) <= TOL_FIELD
+    m = gpu_m(m0)
+    ctx.rk_step(m, 20, 1e-14, method)
+    ctx.sync()
+    ref = mm.run(p, t64(m0), 1e-14, 20, method).numpy()
+    assert np.abs(host(m) - ref).max() <= 1e-4
+
+
 def test_plain_workload_200_rk4_steps_matches_oracle():
     """The plain workload: 32x32x4, random m, RK4 dt = 1e-14 s, 200 steps."""
     from paper_2602_12242_gb300 import inputs
