@@ -81,3 +81,34 @@ def test_coupled_method_converges_at_third_order():
             m = mri.mri_step(p, m, T / n)
         errs.append(float((m - ref).abs().max()))
     assert 6.0 < errs[0] / errs[1] < 11.0 and 6.0 < errs[1] / errs[2] < 11.0, errs
+
+
+def test_evaluation_counts_against_table_2():
+    """Table II (Sec. III-C): RK4 evaluates the full right-hand side (demag and
+    exchange) 4 times per step; the MRI step evaluates demag 3 times, and
+    over the 1.25e-13 s interval RK4 needs 5 steps against MRI's 1.  Exchange
+    per MRI step: 12 fast Knoth-Wolke steps x 3 stages = 36 here; the table
+    prints 37 (the reading of the fast step count is the one difference)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2_eval_counts.json")))
+    p = _problem()
+    m = _m0()
+    calls = {"fast": 0, "slow": 0, "full": 0}
+
+    def counted(name, f):
+        def g_(x):
+            calls[name] += 1
+            return f(x)
+        return g_
+
+    mri.mri_step(p, m, 1e-13, fast=counted("fast", lambda x: mri.fast_rhs(p, x)),
+                 slow=counted("slow", lambda x: mri.slow_rhs(p, x)))
+    assert calls["slow"] == g["mri"]["demag_per_step"] == 3
+    assert calls["fast"] == 36 == g["mri"]["exchange_per_step"] - 1
+    mm.rk4_step(p, m, 1e-14, f=counted("full", lambda x: mm.rhs(p, x)))
+    assert calls["full"] == g["rk4"]["demag_per_step"] == g["rk4"]["exchange_per_step"]
+    steps = {k: round(g["interval_s"] / g[k]["max_dt_s"]) for k in ("rk4", "mri")}
+    assert steps == {"rk4": g["rk4"]["steps"], "mri": g["mri"]["steps"]}
+    assert steps["rk4"] * calls["full"] == g["rk4"]["total_demag"]
+    assert steps["mri"] * calls["slow"] == g["mri"]["total_demag"]
