@@ -296,3 +296,29 @@ def test_fno_inverse_as_the_real_part_of_a_full_inverse_is_caught(monkeypatch):
 def test_fno_filter_transpose_without_conjugation_is_caught(monkeypatch):
     monkeypatch.setattr(fno, "adjoint_filters", lambda R: R.transpose(2, 3).clone())
     planted_fails(pins_fno.test_adjoint_filters_transpose_the_spectral_convolution)
+
+
+# ---------------------------------------------------------------------------
+# discrete adjoint
+# ---------------------------------------------------------------------------
+
+from test_oracle_adjoint import setup  # noqa: E402,F401  (the adjoint pins' module fixture)
+import test_oracle_adjoint as pins_adj  # noqa: E402
+
+
+def test_demag_vjp_without_the_ms_factor_is_caught(monkeypatch, setup):  # noqa: F811
+    def backward(ctx, g):
+        m, Ms = ctx.saved_tensors
+        u = torch.from_numpy(mm._convolve(ctx.p, g.detach().numpy()))
+        return u, (m * u).sum(-1), None
+    monkeypatch.setattr(mm._DemagOp, "backward", staticmethod(backward))
+    planted_fails(pins_adj.test_dot_product_tangent_linear_vs_adjoint, setup)
+
+
+def test_demag_vjp_without_its_ms_gradient_is_caught(monkeypatch, setup):  # noqa: F811
+    def backward(ctx, g):
+        m, Ms = ctx.saved_tensors
+        u = torch.from_numpy(mm._convolve(ctx.p, g.detach().numpy()))
+        return Ms[..., None] * u, torch.zeros_like(Ms), None
+    monkeypatch.setattr(mm._DemagOp, "backward", staticmethod(backward))
+    planted_fails(pins_adj.test_dot_product_tangent_linear_vs_adjoint, setup)
