@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -174,11 +175,37 @@ def algorithmic_bytes(cfg, P, ms_map=False, ku_map=False, axis_map=False):
     }
 
 
-def source_digest():
+CSRC = os.path.join(ROOT, "paper_2602_12242_gb300", "csrc")
+# translation unit that defines each kernel of the traffic table
+KERNEL_TU = {"yz_fused": "demag_plane.cu", "x_fwd": "demag_plane.cu", "x_inv": "demag_plane.cu",
+             "local_stage_rk4_s1": "local.cu"}
+
+
+def kernel_sources(kernel):
+    """The kernel's translation unit and every local header it includes,
+    directly or through other headers (paths relative to the repository)."""
+    todo, seen = [os.path.join(CSRC, KERNEL_TU[kernel])], set()
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in seen:
+            continue
+        seen.add(f)
+        for inc in re.findall(r'^\s*#include\s+"([^"]+)"', open(f).read(), flags=re.M):
+            todo.append(os.path.join(os.path.dirname(f), inc))
+    return sorted(os.path.relpath(f, ROOT) for f in seen)
+
+
+def source_digest(kernel=None):
+    """sha256 (first 16 hex digits) of the sources a kernel is compiled from
+    (names and contents); without a kernel, of every file under csrc/."""
     h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_2602_12242_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    if kernel is None:
+        for f in sorted(os.listdir(CSRC)):
+            h.update(open(os.path.join(CSRC, f), "rb").read())
+    else:
+        for rel in kernel_sources(kernel):
+            h.update(rel.encode())
+            h.update(open(os.path.join(ROOT, rel), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -191,7 +218,7 @@ def load_traffic(workload_name, kernel):
     try:
         d = json.load(open(p))
         e = d.get(workload_name, {}).get(kernel)
-        if e and e.get("source_digest") == source_digest():
+        if e and e.get("source_digest") == source_digest(kernel):
             return e["dram_bytes_per_launch"]
     except Exception:
         pass

@@ -33,7 +33,22 @@ def test_film_spectrum_has_four_tensor_components():
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     entry = t["bulk"]["yz_fused"]
-    monkeypatch.setattr(bench, "source_digest", lambda: entry["source_digest"])
+    monkeypatch.setattr(bench, "source_digest", lambda kernel=None: entry["source_digest"])
     assert bench.load_traffic("bulk", "yz_fused") == entry["dram_bytes_per_launch"]
-    monkeypatch.setattr(bench, "source_digest", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "source_digest", lambda kernel=None: "0" * 16)
     assert bench.load_traffic("bulk", "yz_fused") is None
+
+
+def test_kernel_digests_cover_their_translation_unit_and_headers_only():
+    """A kernel's digest covers the file that defines it and every local
+    header it includes (through other headers too), and nothing else."""
+    plane = bench.kernel_sources("yz_fused")
+    for f in ("paper_2602_12242_gb300/csrc/demag_plane.cu", "paper_2602_12242_gb300/csrc/regfft.cuh",
+              "paper_2602_12242_gb300/csrc/fft.cuh", "paper_2602_12242_gb300/csrc/bulk.cuh",
+              "paper_2602_12242_gb300/csrc/common.cuh", "include/mx.h"):
+        assert f in plane
+    assert not any(f.endswith(("fno.cu", "cnn.cu", "api.cu", "local.cu")) for f in plane)
+    local = bench.kernel_sources("local_stage_rk4_s1")
+    assert "paper_2602_12242_gb300/csrc/local.cuh" in local
+    assert not any(f.endswith("demag_plane.cu") for f in local)
+    assert bench.source_digest("x_fwd") == bench.source_digest("yz_fused") != bench.source_digest("local_stage_rk4_s1")
