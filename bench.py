@@ -195,9 +195,17 @@ def kernel_sources(kernel):
     return sorted(os.path.relpath(f, ROOT) for f in seen)
 
 
+def _code_text(path):
+    """A source file without its comments and with whitespace collapsed, so
+    that comment and layout edits leave the digest alone."""
+    text = re.sub(r"//[^\n]*|/\*.*?\*/", " ", open(path).read(), flags=re.S)
+    return " ".join(text.split())
+
+
 def source_digest(kernel=None):
-    """sha256 (first 16 hex digits) of the sources a kernel is compiled from
-    (names and contents); without a kernel, of every file under csrc/."""
+    """sha256 (first 16 hex digits) of the code a kernel is compiled from
+    (file names and their text without comments); without a kernel, of every
+    file under csrc/ byte for byte."""
     h = hashlib.sha256()
     if kernel is None:
         for f in sorted(os.listdir(CSRC)):
@@ -205,7 +213,7 @@ def source_digest(kernel=None):
     else:
         for rel in kernel_sources(kernel):
             h.update(rel.encode())
-            h.update(open(os.path.join(ROOT, rel), "rb").read())
+            h.update(_code_text(os.path.join(ROOT, rel)).encode())
     return h.hexdigest()[:16]
 
 

@@ -346,8 +346,9 @@ typedef struct mx_fno mx_fno;
 int mx_fno_num_params(int modes);
 
 /* Network for nx x ny fields (2*modes <= nx, ny <= 1024, 1 <= modes <= 16)
- * and batches up to max_batch; allocates all of its buffers (about 2.6 kB
- * per cell of the largest batch).  The parameters start at zero. */
+ * and batches up to max_batch (<= 65535); allocates all of its buffers
+ * (about 2.6 kB per cell of the largest batch).  The parameters start at
+ * zero. */
 mx_status mx_fno_create(mx_fno **out, int nx, int ny, int modes, int max_batch);
 mx_status mx_fno_destroy(mx_fno *net);
 

@@ -619,6 +619,10 @@ static mx_status fno_wgrad(const float* A, int M, int lda, const float* Bv, int 
     set_error("fno_wgrad: column-major A is only supported for the 128 x 32 case");
     return MX_ERR_INVALID_ARG;
   }
+  if (M * (N + 1) > 256 * 17) {  // outputs per thread of the general kernel
+    set_error("fno_wgrad: more than 256 x 17 outputs");
+    return MX_ERR_INVALID_ARG;
+  }
   const size_t sm = (size_t)kWgTile * (M + N + 1) * sizeof(float);
   fno_wgrad_kernel<<<grid, 256, sm, st>>>(A, M, lda, Bv, N, ldb, gelu_b ? 1 : 0, nc, chunk, dW, db);
   return launch_check("fno_wgrad_kernel");
@@ -691,9 +695,11 @@ mx_status mx_fno_destroy(mx_fno* n) {
 
 mx_status mx_fno_create(mx_fno** out, int nx, int ny, int modes, int max_batch) {
   clear_error();
+  // the column passes put the batch on the grid's y axis (at most 65535 blocks)
   if (!out || modes < 1 || modes > kFMaxK || nx < 2 * modes || ny < 2 * modes || nx > kFMaxN || ny > kFMaxN ||
-      max_batch < 1) {
-    set_error("mx_fno_create: need out != NULL, 1 <= modes <= 16, 2*modes <= nx, ny <= 1024 and max_batch >= 1");
+      max_batch < 1 || max_batch > 65535) {
+    set_error("mx_fno_create: need out != NULL, 1 <= modes <= 16, 2*modes <= nx, ny <= 1024 and "
+              "1 <= max_batch <= 65535");
     return MX_ERR_INVALID_ARG;
   }
   *out = nullptr;

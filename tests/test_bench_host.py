@@ -52,3 +52,11 @@ def test_kernel_digests_cover_their_translation_unit_and_headers_only():
     assert "paper_2602_12242_gb300/csrc/local.cuh" in local
     assert not any(f.endswith("demag_plane.cu") for f in local)
     assert bench.source_digest("x_fwd") == bench.source_digest("yz_fused") != bench.source_digest("local_stage_rk4_s1")
+
+
+def test_kernel_digest_ignores_comments_and_layout(tmp_path):
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text("int f(int x) {  // doubles\n  return 2 * x; /* the\n result */\n}\n")
+    b.write_text("int f(int x) {\n return 2 * x;\n}\n")
+    c.write_text("int f(int x) { return 3 * x; }\n")
+    assert bench._code_text(str(a)) == bench._code_text(str(b)) != bench._code_text(str(c))

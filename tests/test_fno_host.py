@@ -20,9 +20,10 @@ def test_parameter_count_matches_the_oracle_layout(lib):
 
 
 @pytest.mark.parametrize("nx,ny,K,B", [(30, 20, 12, 1), (20, 30, 12, 1), (64, 64, 0, 1), (64, 64, 17, 1),
-                                       (2048, 64, 12, 1), (64, 2048, 12, 1), (64, 64, 12, 0)])
+                                       (2048, 64, 12, 1), (64, 2048, 12, 1), (64, 64, 12, 0),
+                                       (64, 64, 12, 65536)])
 def test_create_refuses_grids_without_room_for_the_modes(lib, nx, ny, K, B):
-    """2K <= nx, ny <= 1024, 1 <= K <= 16 and max_batch >= 1, checked before any allocation."""
+    """2K <= nx, ny <= 1024, 1 <= K <= 16 and 1 <= max_batch <= 65535, checked before any allocation."""
     with pytest.raises(lib.MxError) as e:
         lib.mx_fno_create(nx, ny, K, B)
     assert e.value.status == lib.MX_ERR_INVALID_ARG
