@@ -213,8 +213,8 @@ def train(net, M, H, epochs, batch, lr=1e-3, weight_decay=1e-4, milestones=(20, 
     losses = []
     for ep in range(epochs):
         lr_ep = lr * gamma ** sum(ep >= mst for mst in milestones)
-        perm = torch.as_tensor(rng.permutation(n), device="cuda")
-        tot, cnt = torch.zeros(1, device="cuda"), 0
+        perm = torch.as_tensor(rng.permutation(n), device=M.device)
+        tot, cnt = torch.zeros(1, device=M.device), 0
         for s in range(0, n - batch + 1, batch):
             idx = perm[s:s + batch]
             loss, _ = net.loss_grad(M.index_select(0, idx), H.index_select(0, idx), want_grad=False)

@@ -1,0 +1,52 @@
+"""Control flow of the surrogate training loop (CPU only, with a stand-in
+network that records its calls): the step schedule of Sec. II-D (the rate
+halves at epochs 20, 40 and 60), one pass over a fresh permutation of the
+pairs per epoch, and the mean loss per epoch."""
+import numpy as np
+import torch
+
+from paper_2602_12242_gb300.surrogate import normalizer_stats, train
+
+
+class Recorder:
+    def __init__(self):
+        self.lrs, self.seen, self.wd = [], [], set()
+
+    def loss_grad(self, m, h, want_grad=True):
+        self.seen.append(m[:, 0, 0, 0, 0].clone())
+        return torch.tensor([float(m[:, 0, 0, 0, 0].mean())]), None
+
+    def adam_step(self, lr, weight_decay):
+        self.lrs.append(lr)
+        self.wd.add(weight_decay)
+
+
+def test_schedule_batches_and_epoch_losses():
+    n, batch, epochs = 12, 4, 70
+    M = torch.zeros((n, 1, 2, 2, 4))
+    M[:, 0, 0, 0, 0] = torch.arange(n, dtype=torch.float32)
+    net = Recorder()
+    losses = train(net, M, M.clone(), epochs=epochs, batch=batch, lr=1e-3, weight_decay=1e-4, seed=3)
+    steps = n // batch
+    assert len(net.lrs) == epochs * steps and net.wd == {1e-4}
+    lr_at = [net.lrs[e * steps] for e in range(epochs)]
+    assert lr_at[0] == lr_at[19] == 1e-3
+    assert lr_at[20] == lr_at[39] == 5e-4
+    assert lr_at[40] == 2.5e-4 and lr_at[60] == lr_at[69] == 1.25e-4
+    for e in range(epochs):
+        seen = torch.cat(net.seen[e * steps:(e + 1) * steps])
+        assert sorted(seen.tolist()) == list(range(n))  # every pair once per epoch
+        assert abs(losses[e] - float(seen.mean())) < 1e-6
+    assert not torch.equal(torch.cat(net.seen[:steps]), torch.cat(net.seen[steps:2 * steps]))
+
+
+def test_normalizer_statistics_per_component():
+    rng = np.random.default_rng(4)
+    M = torch.from_numpy(rng.normal(size=(5, 1, 3, 4, 4)).astype(np.float32))
+    H = torch.from_numpy(rng.normal(size=(5, 1, 3, 4, 4)).astype(np.float32) * 7 + 2)
+    st = normalizer_stats(M, H)
+    m = M[..., :3].reshape(-1, 3).double()
+    h = H[..., :3].reshape(-1, 3).double()
+    ref = m.mean(0).tolist() + m.std(0, unbiased=False).tolist() + h.mean(0).tolist() + \
+        h.std(0, unbiased=False).tolist()
+    assert np.allclose(st, ref, rtol=1e-12)
