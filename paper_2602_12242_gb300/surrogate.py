@@ -20,6 +20,21 @@ from .solver import to_dev4
 CHANNELS = (3, 32, 64, 32, 3)
 
 
+def _fields(shape, max_batch, *ts):
+    """Batch size of float4 field tensors of one grid (nz, ny, nx): (B, nz, ny,
+    nx, 4) or one (nz, ny, nx, 4) field; contiguous CUDA float32, 1 <= B <=
+    max_batch.  The library takes plain pointers, so the sizes are checked here."""
+    one = tuple(shape) + (4,)
+    b = None
+    for t in ts:
+        ok = t.dtype == torch.float32 and t.is_cuda and t.is_contiguous()
+        tb = 1 if tuple(t.shape) == one else (t.shape[0] if t.dim() == 5 and tuple(t.shape[1:]) == one else None)
+        if not ok or tb is None or (b is not None and tb != b) or not 1 <= tb <= max_batch:
+            raise ValueError(f"expected contiguous CUDA float32 fields of shape (B,) + {one}, 1 <= B <= {max_batch}")
+        b = tb
+    return b
+
+
 def init_params(seed):
     """Seeded initial parameters: each layer's weights and biases uniform in
     +-1/sqrt(fan_in) (fan_in = 27 * input channels), in the library's order."""
@@ -70,22 +85,26 @@ class Surrogate:
         L.mx_cnn_set_normalizer(self.h, self.stats)
 
     def forward(self, m):
-        b = m.shape[0] if m.dim() == 5 else 1
+        m = m.contiguous()
+        b = _fields(self.shape, self.max_batch, m)
         h = torch.empty_like(m)
-        L.mx_cnn_forward(self.h, m.contiguous(), h, b)
+        L.mx_cnn_forward(self.h, m, h, b)
         return h
 
     def loss_grad(self, m, h_target, want_grad=True):
-        b = m.shape[0] if m.dim() == 5 else 1
+        m, h_target = m.contiguous(), h_target.contiguous()
+        b = _fields(self.shape, self.max_batch, m, h_target)
         loss = torch.empty(1, dtype=torch.float32, device="cuda")
         grad = torch.empty(self.n_params, dtype=torch.float32, device="cuda") if want_grad else None
-        L.mx_cnn_loss_grad(self.h, m.contiguous(), h_target.contiguous(), b, loss, grad)
+        L.mx_cnn_loss_grad(self.h, m, h_target, b, loss, grad)
         return loss, grad
 
     def adam_step(self, lr, weight_decay):
         L.mx_cnn_adam_step(self.h, lr, weight_decay)
 
     def forward_into(self, m, h, batch):
+        if _fields(self.shape, self.max_batch, m, h) < batch:
+            raise ValueError("batch larger than the tensors")
         L.mx_cnn_forward(self.h, m, h, batch)
 
     def attach(self, ctx_h):
@@ -156,19 +175,23 @@ class FourierSurrogate:
         L.mx_fno_set_normalizer(self.h, self.stats)
 
     def forward(self, m):
-        b = m.shape[0] if m.dim() == 5 else 1
+        m = m.contiguous()
+        b = _fields(self.shape, self.max_batch, m)
         h = torch.empty_like(m)
-        L.mx_fno_forward(self.h, m.contiguous(), h, b)
+        L.mx_fno_forward(self.h, m, h, b)
         return h
 
     def forward_into(self, m, h, batch):
+        if _fields(self.shape, self.max_batch, m, h) < batch:
+            raise ValueError("batch larger than the tensors")
         L.mx_fno_forward(self.h, m, h, batch)
 
     def loss_grad(self, m, h_target, want_grad=True):
-        b = m.shape[0] if m.dim() == 5 else 1
+        m, h_target = m.contiguous(), h_target.contiguous()
+        b = _fields(self.shape, self.max_batch, m, h_target)
         loss = torch.empty(1, dtype=torch.float32, device="cuda")
         grad = torch.empty(self.n_params, dtype=torch.float32, device="cuda") if want_grad else None
-        L.mx_fno_loss_grad(self.h, m.contiguous(), h_target.contiguous(), b, loss, grad)
+        L.mx_fno_loss_grad(self.h, m, h_target, b, loss, grad)
         return loss, grad
 
     def adam_step(self, lr, weight_decay):

@@ -50,3 +50,38 @@ def test_normalizer_statistics_per_component():
     ref = m.mean(0).tolist() + m.std(0, unbiased=False).tolist() + h.mean(0).tolist() + \
         h.std(0, unbiased=False).tolist()
     assert np.allclose(st, ref, rtol=1e-12)
+
+
+class FakeField:
+    """Stands in for a CUDA tensor in the wrappers' size checks."""
+
+    def __init__(self, shape, dtype=torch.float32, cuda=True, contiguous=True):
+        self.shape, self.dtype, self.is_cuda, self._c = torch.Size(shape), dtype, cuda, contiguous
+
+    def dim(self):
+        return len(self.shape)
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_wrappers_check_field_sizes_before_the_library():
+    import pytest
+    from paper_2602_12242_gb300.surrogate import _fields
+    g = (1, 32, 48)
+    assert _fields(g, 4, FakeField((1, 32, 48, 4))) == 1
+    assert _fields(g, 4, FakeField((3, 1, 32, 48, 4)), FakeField((3, 1, 32, 48, 4))) == 3
+    assert _fields(g, 4, FakeField((1, 32, 48, 4)), FakeField((1, 1, 32, 48, 4))) == 1
+    bad = [
+        [FakeField((5, 1, 32, 48, 4))],                                   # above max_batch
+        [FakeField((0, 1, 32, 48, 4))],                                   # empty batch
+        [FakeField((1, 32, 47, 4))],                                      # another grid
+        [FakeField((2, 1, 32, 48, 3))],                                   # float3 records
+        [FakeField((2, 1, 32, 48, 4)), FakeField((3, 1, 32, 48, 4))],     # batches differ
+        [FakeField((1, 32, 48, 4), dtype=torch.float64)],
+        [FakeField((1, 32, 48, 4), cuda=False)],
+        [FakeField((1, 32, 48, 4), contiguous=False)],
+    ]
+    for ts in bad:
+        with pytest.raises(ValueError):
+            _fields(g, 4, *ts)
