@@ -90,14 +90,28 @@ class Context:
     def build_demag_kernel(self, stream=None):
         L.mx_build_demag_kernel(self.h, stream)
 
+    def _check_map(self, t, rec):
+        """A per-cell map: contiguous CUDA float32 of shape (nz, ny, nx) (+ (4,) for float4 records)."""
+        shape = self.shape + rec
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != shape:
+            raise ValueError(f"expected contiguous CUDA float32 tensor of shape {shape}")
+
     def set_ms_map(self, ms, stream=None):
-        L.mx_set_ms_map(self.h, None if ms is None else ms.contiguous(), stream)
+        if ms is not None:
+            ms = ms.contiguous()
+            self._check_map(ms, ())
+        L.mx_set_ms_map(self.h, ms, stream)
         if stream is None:
             torch.cuda.current_stream().synchronize()
 
     def set_anis_map(self, ku, axis, stream=None):
-        L.mx_set_anis_map(self.h, None if ku is None else ku.contiguous(),
-                          None if axis is None else axis.contiguous(), stream)
+        if ku is not None:
+            ku = ku.contiguous()
+            self._check_map(ku, ())
+        if axis is not None:
+            axis = axis.contiguous()
+            self._check_map(axis, (4,))
+        L.mx_set_anis_map(self.h, ku, axis, stream)
         if stream is None:
             torch.cuda.current_stream().synchronize()
 

@@ -85,3 +85,17 @@ def test_wrappers_check_field_sizes_before_the_library():
     for ts in bad:
         with pytest.raises(ValueError):
             _fields(g, 4, *ts)
+
+
+def test_material_maps_are_checked_against_the_grid():
+    import types
+
+    import pytest
+    from paper_2602_12242_gb300.solver import Context
+    me = types.SimpleNamespace(shape=(2, 3, 4))
+    Context._check_map(me, FakeField((2, 3, 4)), ())
+    Context._check_map(me, FakeField((2, 3, 4, 4)), (4,))
+    for t, rec in [(FakeField((2, 3, 5)), ()), (FakeField((24,)), ()), (FakeField((2, 3, 4, 3)), (4,)),
+                   (FakeField((2, 3, 4), dtype=torch.float64), ()), (FakeField((2, 3, 4), cuda=False), ())]:
+        with pytest.raises(ValueError):
+            Context._check_map(me, t, rec)
