@@ -1,7 +1,9 @@
-"""Control flow of the surrogate training loop (CPU only, with a stand-in
-network that records its calls): the step schedule of Sec. II-D (the rate
-halves at epochs 20, 40 and 60), one pass over a fresh permutation of the
-pairs per epoch, and the mean loss per epoch."""
+"""Host-side logic of the Python layer (CPU only): the surrogate training
+loop's control flow with a stand-in network that records its calls (the step
+schedule of Sec. II-D, halving the rate at epochs 20, 40 and 60; one pass
+over a fresh permutation of the pairs per epoch; the mean loss per epoch),
+and the size checks the wrappers make before handing pointers to the
+library."""
 import numpy as np
 import torch
 
