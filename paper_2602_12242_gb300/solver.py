@@ -22,6 +22,24 @@ def from_dev4(t):
     return t[..., :3].double().cpu().numpy()
 
 
+def save_state(path, m, t=0.0, step=0, meta=None):
+    """Checkpoint of a run: the xyz of the float4 field m (any device; the
+    FP32 values are stored exactly; the w slot, which mx_rk_step does not
+    read, is not kept), the simulated time t [s], the step count and a
+    JSON-serialisable dict of run metadata, in one .npz file."""
+    import json
+    np.savez(path, m=m[..., :3].float().cpu().numpy(), t=np.float64(t), step=np.int64(step),
+             meta=np.array(json.dumps(meta or {})))
+
+
+def load_state(path, device="cuda"):
+    """(m, t, step, meta) from save_state; m as a float4 tensor on `device`."""
+    import json
+    with np.load(path) as d:
+        m = to_dev4(d["m"], device)
+        return m, float(d["t"]), int(d["step"]), json.loads(str(d["meta"]))
+
+
 _METHODS = {"rk4": L.MX_RK4, "euler": L.MX_EULER, "mri": L.MX_MRI}
 
 

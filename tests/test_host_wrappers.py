@@ -101,3 +101,17 @@ def test_material_maps_are_checked_against_the_grid():
                    (FakeField((2, 3, 4), dtype=torch.float64), ()), (FakeField((2, 3, 4), cuda=False), ())]:
         with pytest.raises(ValueError):
             Context._check_map(me, t, rec)
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """save_state / load_state keep the field bit for bit (FP32), the time,
+    the step count and the metadata."""
+    from paper_2602_12242_gb300.solver import load_state, save_state, to_dev4
+    rng = np.random.default_rng(8)
+    a = rng.normal(size=(2, 3, 5, 3))
+    m = to_dev4(a / np.linalg.norm(a, axis=-1, keepdims=True), device="cpu")
+    path = tmp_path / "run.npz"
+    save_state(path, m, t=1.25e-10, step=2500, meta={"workload": "film", "dt": 5e-14})
+    m2, t, step, meta = load_state(path, device="cpu")
+    assert torch.equal(m2, m) and m2.shape == (2, 3, 5, 4)
+    assert t == 1.25e-10 and step == 2500 and meta == {"workload": "film", "dt": 5e-14}
