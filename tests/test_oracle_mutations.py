@@ -144,6 +144,36 @@ def test_tensor_with_a_wrong_self_factor_is_caught(monkeypatch):
     planted_fails(pins_tensor.test_self_term_trace_one_and_matches_aharoni, (1, 2, 3))
 
 
+def test_full_tensor_with_a_wrong_parity_is_caught(monkeypatch):
+    """N_xy taken as even in X when the octant is unfolded to signed offsets:
+    the operator loses its symmetry and the unfolded and octant-based sums
+    disagree."""
+    orig = tn.tensor_full
+
+    def full(nx, ny, nz, dx, dy, dz):
+        f = orig(nx, ny, nz, dx, dy, dz)
+        x = np.arange(-(nx - 1), nx)
+        f[3] = f[3] * (np.sign(x) + (x == 0))[None, None, :]
+        return f
+    monkeypatch.setattr(tn, "tensor_full", full)
+    planted_fails(pins_fields.test_linear_operator_is_ms_weighted_symmetric, False)
+    planted_fails(pins_tensor.test_fft_convolution_equals_direct_sum, (3, 5, 2))
+
+
+def test_full_tensor_without_any_parity_is_caught(monkeypatch):
+    """Every component unfolded as even: still symmetric, but the prism sum of
+    a uniform field no longer gives Aharoni's factors."""
+    orig = tn.tensor_full
+
+    def full(nx, ny, nz, dx, dy, dz):
+        f = orig(nx, ny, nz, dx, dy, dz)
+        o = f[:, nz - 1:nz, ny - 1:ny, nx - 1:nx]
+        return np.abs(f) * np.where(o < 0, -1.0, 1.0)
+    monkeypatch.setattr(tn, "tensor_full", full)
+    planted_fails(pins_tensor.test_uniform_magnetisation_energy_equals_prism_factor, (6, 5, 4),
+                  (2e-9, 2e-9, 2e-9))
+
+
 # ---------------------------------------------------------------------------
 # LLG and time stepping
 # ---------------------------------------------------------------------------
