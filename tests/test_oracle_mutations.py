@@ -79,6 +79,29 @@ def test_chiral_ghost_with_the_wrong_sign_is_caught(monkeypatch):
     planted_fails(pins_fields.test_linear_operator_is_ms_weighted_symmetric, True)
 
 
+def test_chiral_ghost_at_the_wrong_distance_is_caught(monkeypatch):
+    """The y-face ghosts built with dx instead of dy (cells are not cubes)."""
+    orig = mm.ghosted
+
+    def ghosted(p, m):
+        q = mm.Problem(p.nx, p.ny, p.nz, p.dx, p.dx, p.dz, Ms=p.Ms, A=p.A, Ku=p.Ku, ku_axis=p.ku_axis, D=p.D,
+                       alpha=p.alpha, gamma=p.gamma, h_bias=p.h_bias, dmi=p.dmi, demag=p.demag)
+        return orig(q, m)
+    monkeypatch.setattr(mm, "ghosted", ghosted)
+    planted_fails(pins_fields.test_heff_is_energy_gradient)
+
+
+def test_demag_energy_without_its_half_is_caught(monkeypatch):
+    orig = mm.energies
+
+    def energies(p, m):
+        e = orig(p, m)
+        e["demag"] *= 2.0
+        return e
+    monkeypatch.setattr(mm, "energies", energies)
+    planted_fails(pins_fields.test_heff_is_energy_gradient)
+
+
 def test_anisotropy_with_Ku_for_2Ku_is_caught(monkeypatch):
     orig = mm.anisotropy_field
     monkeypatch.setattr(mm, "anisotropy_field", lambda p, m: 0.5 * orig(p, m))
@@ -236,6 +259,11 @@ def test_rk4_without_renormalisation_is_caught(monkeypatch):
     planted_fails(pins_fields.test_energy_decays_and_norm_conserved_plain)
 
 
+def test_normalisation_by_the_squared_norm_is_caught(monkeypatch):
+    monkeypatch.setattr(mm, "normalize", lambda m: m / (m * m).sum(-1, keepdim=True))
+    planted_fails(pins_fields.test_energy_decays_and_norm_conserved_plain)
+
+
 def test_central_exchange_energy_with_a_one_sided_step_is_caught(monkeypatch):
     orig = mm.exchange_energy_central
     monkeypatch.setattr(mm, "exchange_energy_central", lambda p, m: 4.0 * orig(p, m))
@@ -266,6 +294,11 @@ def test_mri_forcing_without_the_difference_of_rows_is_caught(monkeypatch):
         return Y[3]
     monkeypatch.setattr(mri, "mri_step", mri_step)
     planted_fails(pins_mri.test_without_fast_part_it_is_the_single_rate_method)
+
+
+def test_fast_step_count_rounded_down_is_caught(monkeypatch):
+    monkeypatch.setattr(mri, "fast_steps", lambda interval, ratio: max(1, math.floor(interval / ratio)))
+    planted_fails(pins_mri.test_fast_step_counts)
 
 
 def test_knoth_wolke_with_a_wrong_weight_is_caught(monkeypatch):
