@@ -385,3 +385,55 @@ def test_demag_vjp_without_its_ms_gradient_is_caught(monkeypatch, setup):  # noq
         return Ms[..., None] * u, torch.zeros_like(Ms), None
     monkeypatch.setattr(mm._DemagOp, "backward", staticmethod(backward))
     planted_fails(pins_adj.test_dot_product_tangent_linear_vs_adjoint, setup)
+
+
+def _planted_gradient(state_offset=0, skip_normalisation=False, ms_last_step_only=False):
+    """The oracle's reverse sweep with one planted mistake."""
+    from oracle import adjoint as adj
+
+    def gradient(p, m0_raw, dt, nsteps, objective):
+        m0_raw = mm.as_t(m0_raw).detach()
+        Ms = mm.ms_field(p).detach().clone()
+        states = adj.forward_states(adj._with_ms(p, Ms), m0_raw, dt, nsteps)
+        mT = states[-1].detach().requires_grad_(True)
+        J = objective(mT)
+        lam, = torch.autograd.grad(J, mT)
+        g_ms = torch.zeros_like(Ms)
+        for s in range(nsteps - 1, -1, -1):
+            ms_var = Ms.clone().requires_grad_(True)
+            q = adj._with_ms(p, ms_var)
+            ms_in = states[s + state_offset].detach().requires_grad_(True)
+            out = mm.rk4_step(q, ms_in, dt)
+            lam, gms = torch.autograd.grad(out, (ms_in, ms_var), grad_outputs=lam)
+            g_ms = gms if ms_last_step_only else g_ms + gms
+        if skip_normalisation:
+            return float(J.detach()), lam.detach(), g_ms.detach()
+        raw = m0_raw.clone().requires_grad_(True)
+        g_raw, = torch.autograd.grad(mm.normalize(raw), raw, grad_outputs=lam)
+        return float(J.detach()), g_raw.detach(), g_ms.detach()
+    return gradient
+
+
+def test_reverse_sweep_on_the_wrong_stored_state_is_caught(monkeypatch, setup):  # noqa: F811
+    from oracle import adjoint as adj
+    monkeypatch.setattr(adj, "gradient", _planted_gradient(state_offset=1))
+    planted_fails(pins_adj.test_dot_product_tangent_linear_vs_adjoint, setup)
+
+
+def test_gradient_without_the_initial_normalisation_is_caught(monkeypatch, setup):  # noqa: F811
+    from oracle import adjoint as adj
+    monkeypatch.setattr(adj, "gradient", _planted_gradient(skip_normalisation=True))
+    planted_fails(pins_adj.test_dot_product_tangent_linear_vs_adjoint, setup)
+
+
+def test_ms_gradient_of_the_last_step_only_is_caught(monkeypatch, setup):  # noqa: F811
+    from oracle import adjoint as adj
+    monkeypatch.setattr(adj, "gradient", _planted_gradient(ms_last_step_only=True))
+    planted_fails(pins_adj.test_dot_product_tangent_linear_vs_adjoint, setup)
+
+
+def test_planted_gradient_without_a_mistake_passes(monkeypatch, setup):  # noqa: F811
+    """Control: the planting helper itself reproduces the oracle's sweep."""
+    from oracle import adjoint as adj
+    monkeypatch.setattr(adj, "gradient", _planted_gradient())
+    pins_adj.test_dot_product_tangent_linear_vs_adjoint(setup)
