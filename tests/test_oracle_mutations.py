@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+import test_oracle_adjoint as pins_adj
 import test_oracle_cnn as pins_cnn
 import test_oracle_fields as pins_fields
 import test_oracle_fno as pins_fno
@@ -20,6 +21,7 @@ import test_oracle_tensor as pins_tensor
 from oracle import cnn, fno, mri
 from oracle import micromag as mm
 from oracle import tensor as tn
+from test_oracle_adjoint import setup  # noqa: F401  (the adjoint pins' module fixture)
 
 
 def planted_fails(pin, *args):
@@ -365,8 +367,6 @@ def test_fno_filter_transpose_without_conjugation_is_caught(monkeypatch):
 # discrete adjoint
 # ---------------------------------------------------------------------------
 
-from test_oracle_adjoint import setup  # noqa: E402,F401  (the adjoint pins' module fixture)
-import test_oracle_adjoint as pins_adj  # noqa: E402
 
 
 def test_demag_vjp_without_the_ms_factor_is_caught(monkeypatch, setup):  # noqa: F811
