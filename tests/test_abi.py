@@ -72,3 +72,17 @@ def test_null_arguments_rejected_without_gpu(libmx):
     assert b"NULL" in L.mx_last_error()
     assert L.mx_heff(None, None, None, 31, None) == _lib.MX_ERR_INVALID_ARG
     assert L.mx_destroy(None) == _lib.MX_OK
+
+
+def test_header_is_strict_c99_and_cxx11(tmp_path):
+    """include/mx.h is usable from plain C (C99, pedantic, warnings as errors)
+    and from C++ with no CUDA or torch headers."""
+    import subprocess
+    c = tmp_path / "use.c"
+    c.write_text('#include "mx.h"\nint main(void) { mx_ctx *c = 0; return mx_destroy(c); }\n')
+    subprocess.run(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                    os.path.join(ROOT, "include"), str(c)], check=True)
+    cc = tmp_path / "use.cpp"
+    cc.write_text('#include "mx.h"\nint main() { mx_ctx *c = nullptr; return mx_destroy(c); }\n')
+    subprocess.run(["g++", "-std=c++11", "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                    os.path.join(ROOT, "include"), str(cc)], check=True)
