@@ -86,3 +86,33 @@ def test_header_is_strict_c99_and_cxx11(tmp_path):
     cc.write_text('#include "mx.h"\nint main() { mx_ctx *c = nullptr; return mx_destroy(c); }\n')
     subprocess.run(["g++", "-std=c++11", "-pedantic", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
                     os.path.join(ROOT, "include"), str(cc)], check=True)
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path, libmx):
+    """A C program (no Python, no torch) links libmx.so and makes the calls
+    that need no device: version, parameter counts, argument refusals."""
+    import subprocess
+    from paper_2602_12242_gb300 import build
+    src = tmp_path / "client.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "mx.h"
+int main(void) {
+  mx_params p;
+  mx_ctx *ctx = 0;
+  mx_fno *net = 0;
+  memset(&p, 0, sizeof p);
+  p.nx = 0; p.ny = 8; p.nz = 1; p.dx = p.dy = p.dz = 2e-9; p.Ms = 8e5; p.gamma = 2.211e5;
+  if (mx_create(&ctx, &p) != MX_ERR_UNSUPPORTED || ctx) return 1;
+  if (mx_fno_create(&net, 30, 20, 12, 1) != MX_ERR_INVALID_ARG || net) return 2;
+  printf("%s|%d|%d|%s\n", mx_version(), mx_cnn_num_params(), mx_fno_num_params(12), mx_last_error());
+  return 0;
+}
+''')
+    lib = build.LIB
+    exe = tmp_path / "client"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), lib,
+                    "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.strip().split("|")
+    assert "sm_103a" in out[0] and out[1] == "115907" and out[2] == "2368259" and "mx_fno_create" in out[3]
