@@ -110,3 +110,24 @@ def test_kept_modes_need_room():
     with pytest.raises(AssertionError):
         fno.spectral_conv(torch.zeros(1, 1, 5, 8, dtype=torch.float64), torch.zeros(6, 3, 1, 1, 2,
                                                                                      dtype=torch.float64), 3)
+
+
+@pytest.mark.parametrize("H,W,K", [(8, 10, 3), (9, 7, 2), (6, 6, 3)])
+def test_filter_gradient_closed_form(H, W, K):
+    """dL/dR for L = <g, K_R v> equals c_kx / (H W) * sum_b conj(X[b, i]) X_g[b, o]
+    per kept mode (X, X_g: truncated rfft2 of v and g; c_0 = 1, c_kx = 2):
+    the formula the GPU backward evaluates, against autograd of the oracle."""
+    rng = np.random.default_rng(65)
+    B, Ci, Co = 2, 3, 4
+    v = torch.from_numpy(rng.normal(size=(B, Ci, H, W)))
+    g = torch.from_numpy(rng.normal(size=(B, Co, H, W)))
+    R = rand_R(rng, K, Ci, Co).requires_grad_(True)
+    (fno.spectral_conv(v, R, K) * g).sum().backward()
+    rows = fno.kept_rows(H, K)
+    X = torch.fft.rfft2(v)[:, :, rows, :K]   # (B, Ci, 2K, K)
+    Xg = torch.fft.rfft2(g)[:, :, rows, :K]  # (B, Co, 2K, K)
+    c = torch.full((K,), 2.0, dtype=torch.float64)
+    c[0] = 1.0
+    dR = torch.einsum("bimn,bomn->mnio", X.conj(), Xg) * c.view(1, K, 1, 1) / (H * W)
+    ref = torch.stack([dR.real, dR.imag], dim=-1)
+    assert torch.allclose(R.grad, ref, rtol=1e-10, atol=1e-12 * float(ref.abs().max()))
