@@ -73,3 +73,17 @@ def test_normalizer_round_trip():
     assert torch.allclose(e.mean(0), torch.zeros(3, dtype=torch.float64), atol=1e-12)
     assert torch.allclose(e.std(0, unbiased=False), torch.ones(3, dtype=torch.float64), atol=1e-12)
     assert torch.allclose(n.decode(n.encode(a)), torch.as_tensor(a), atol=1e-12)
+
+
+def test_input_gradient_is_a_convolution_with_flipped_transposed_weights():
+    """dL/dx of y = conv3d(x, W) (3x3x3, zero padding 1) equals conv3d(dL/dy, W')
+    with W'[ci][co][dz][dy][dx] = W[co][ci][2-dz][2-dy][2-dx]: the layout the
+    GPU backward pass packs its weights in."""
+    rng = np.random.default_rng(44)
+    x = torch.from_numpy(rng.normal(size=(2, 3, 3, 5, 4))).requires_grad_(True)
+    W = torch.from_numpy(rng.normal(size=(4, 3, 3, 3, 3)))
+    g = torch.from_numpy(rng.normal(size=(2, 4, 3, 5, 4)))
+    (torch.nn.functional.conv3d(x, W, padding=1) * g).sum().backward()
+    Wf = W.flip(2, 3, 4).transpose(0, 1).contiguous()
+    ref = torch.nn.functional.conv3d(g, Wf, padding=1)
+    assert torch.allclose(x.grad, ref, atol=1e-12)
