@@ -66,3 +66,40 @@ def test_dot_product_tangent_linear_vs_adjoint(setup):
         lhs = float((tl * w).sum())
         rhs = float((gw_m * torch.from_numpy(dm)).sum() + (gw_ms * torch.from_numpy(ds)).sum())
         assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+
+
+@pytest.mark.parametrize("precession", [True, False])
+def test_llg_vector_jacobian_products_closed_form(precession):
+    """For f = c [m x H + alpha m x (m x H)], c = -gamma0/(1+alpha^2), and a
+    cotangent v, the products the GPU adjoint kernel evaluates:
+      d/dm: c [alpha ((m.H) v + (v.m) H - 2 (v.H) m) + H x v]
+      d/dH: c [alpha ((v.m) m - (m.m) v) + v x m]
+    (cross-product terms only with precession), against autograd of the
+    oracle's llg_rhs; m need not be a unit vector."""
+    rng = np.random.default_rng(23)
+    p = mm.Problem(3, 2, 1, 2e-9, 2e-9, 2e-9, alpha=0.27, precession=precession)
+    m = torch.from_numpy(rng.normal(size=(1, 2, 3, 3))).requires_grad_(True)
+    H = torch.from_numpy(rng.normal(size=(1, 2, 3, 3)) * 1e4).requires_grad_(True)
+    v = torch.from_numpy(rng.normal(size=(1, 2, 3, 3)))
+    gm, gH = torch.autograd.grad(mm.llg_rhs(p, m, H), (m, H), grad_outputs=v)
+    m_, H_ = m.detach(), H.detach()
+    dot = lambda a, b: (a * b).sum(-1, keepdim=True)  # noqa: E731
+    c = -p.gamma / (1 + p.alpha ** 2)
+    ref_m = p.alpha * (dot(m_, H_) * v + dot(v, m_) * H_ - 2 * dot(v, H_) * m_)
+    ref_H = p.alpha * (dot(v, m_) * m_ - dot(m_, m_) * v)
+    if precession:
+        ref_m = ref_m + torch.linalg.cross(H_, v, dim=-1)
+        ref_H = ref_H + torch.linalg.cross(v, m_, dim=-1)
+    assert torch.allclose(gm, c * ref_m, rtol=1e-12, atol=1e-12 * float((c * ref_m).abs().max()))
+    assert torch.allclose(gH, c * ref_H, rtol=1e-12, atol=1e-12 * float((c * ref_H).abs().max()))
+
+
+def test_renormalisation_vector_jacobian_product_closed_form():
+    """d(u/|u|)^T v = (v - (n.v) n) / |u| with n = u/|u|."""
+    rng = np.random.default_rng(24)
+    u = torch.from_numpy(rng.normal(size=(4, 3))).requires_grad_(True)
+    v = torch.from_numpy(rng.normal(size=(4, 3)))
+    g, = torch.autograd.grad(mm.normalize(u), u, grad_outputs=v)
+    r = u.detach().norm(dim=-1, keepdim=True)
+    n = u.detach() / r
+    assert torch.allclose(g, (v - (n * v).sum(-1, keepdim=True) * n) / r, rtol=1e-12, atol=1e-14)
