@@ -177,8 +177,8 @@ def algorithmic_bytes(cfg, P, ms_map=False, ku_map=False, axis_map=False):
 
 CSRC = os.path.join(ROOT, "paper_2602_12242_gb300", "csrc")
 # translation unit that defines each kernel of the traffic table
-KERNEL_TU = {"yz_fused": "demag_plane.cu", "x_fwd": "demag_plane.cu", "x_inv": "demag_plane.cu",
-             "local_stage_rk4_s1": "local.cu"}
+KERNEL_TU = {"yzq_kernel": "demag_quad.cu", "yzh_kernel": "demag_plane.cu", "xfk_kernel": "demag_plane.cu",
+             "xik_kernel": "demag_plane.cu", "local_kernel": "local.cu"}
 
 
 def kernel_sources(kernel):
@@ -291,17 +291,19 @@ def run_mx(args, rank, world, local, name, with_extras=True):
     per_step = (launches - 1) / K  # one normalisation per call
     res["launches_per_step"] = per_step
     res["gpu_launches"] = int(round(per_step * K)) + 1
+    names = ctx.kernel_names()
     dom = max(prof, key=lambda k: prof[k][0])
     tot = sum(v[0] for v in prof.values())
-    kern = {k: {"ms_total": round(v[0], 4), "launches": v[1], "share": round(v[0] / tot, 4),
+    kern = {k: {"kernel": names.get(k, k), "ms_total": round(v[0], 4), "launches": v[1],
+                "share": round(v[0] / tot, 4),
                 "us_per_launch": round(1e3 * v[0] / v[1], 3),
                 "gbs": round(ab.get(k, 0) / (1e-3 * v[0] / v[1]) / 1e9, 1)} for k, v in prof.items()}
     res["kernels"] = kern
     peak, src = peaks()
     achieved = ab[dom] / (1e-3 * prof[dom][0] / prof[dom][1]) / 1e9
-    res["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                       "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                       "traffic": load_traffic(name, dom),
+    res["roofline"] = {"bound": "hbm", "kernel": names.get(dom, dom), "slot": dom, "achieved": round(achieved, 1),
+                       "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                       "traffic": load_traffic(name, names.get(dom, dom)),
                        "algorithmic_bytes_per_launch": ab[dom]}
     demag = [k for k in prof if k in ("x_fwd", "y_fwd", "z_mul", "y_inv", "yz_fused", "x_inv")]
     dbytes = sum(ab[k] * prof[k][1] for k in demag)

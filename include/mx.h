@@ -70,8 +70,11 @@ typedef enum {
  *   demag_path  schedule of the demag convolution (same result up to FP32
  *           rounding): MX_DEMAG_AUTO picks the fastest that fits the grid;
  *           MX_DEMAG_GENERIC forces the size-generic separate passes;
- *           MX_DEMAG_PLANE forces the per-kx-plane kernel (MX_ERR_UNSUPPORTED
- *           at mx_create if the grid does not fit it)
+ *           MX_DEMAG_PLANE forces the per-kx-plane kernels (the y/z kernel
+ *           on a cluster of four CTAs per plane where it fits, else the one
+ *           on two CTAs; MX_ERR_UNSUPPORTED at mx_create if the grid fits
+ *           neither); MX_DEMAG_PLANE_PAIR forces the per-kx-plane path with
+ *           the two-CTA y/z kernel
  *   fft_mode  MX_FFT_FP32 (default): every FFT stage in FP32 on the CUDA
  *           cores; MX_FFT_SPLIT_BF16: the first radix-32 stage of the x
  *           transforms runs as a DFT-as-GEMM on the tensor cores with operands
@@ -97,7 +100,7 @@ typedef struct {
 } mx_params;
 
 /* Demag convolution schedules for mx_params.demag_path. */
-enum { MX_DEMAG_AUTO = 0, MX_DEMAG_GENERIC = 1, MX_DEMAG_PLANE = 2 };
+enum { MX_DEMAG_AUTO = 0, MX_DEMAG_GENERIC = 1, MX_DEMAG_PLANE = 2, MX_DEMAG_PLANE_PAIR = 3 };
 
 /* Arithmetic of the demag FFT stages for mx_params.fft_mode. */
 enum { MX_FFT_FP32 = 0, MX_FFT_SPLIT_BF16 = 1 };
@@ -256,13 +259,20 @@ mx_status mx_demag_spectrum(mx_ctx *ctx, float *out, mx_stream_t stream);
 
 /* Kernel timing for profiling: runs `nsteps` steps exactly like
  * mx_rk_step but launches every kernel directly (no graph) with a CUDA event
- * pair around each launch, then synchronises.  For kernel index q in
+ * pair around each launch, then synchronises.  For timing slot q in
  * [0, *n_kernels), ms_total[q] and launches[q] receive the summed duration and
- * the launch count; names via mx_kernel_name(q).  Arrays hold max_kernels. */
+ * the launch count.  Arrays hold max_kernels.
+ *   mx_kernel_slot(q)         the slot's role in the step ("x_fwd",
+ *                             "yz_fused" for the y/z passes, "x_inv",
+ *                             "local_stage", ...), the same for every context;
+ *   mx_kernel_name(ctx, q)    the kernel that this context's schedule
+ *                             launches in that slot (e.g. "yzq_kernel");
+ *                             "" for an unknown slot or a NULL ctx. */
 mx_status mx_profile_step(mx_ctx *ctx, float *m, int nsteps, double dt, int method,
                           mx_stream_t stream, double *ms_total, int *launches,
                           int max_kernels, int *n_kernels);
-const char *mx_kernel_name(int q);
+const char *mx_kernel_slot(int q);
+const char *mx_kernel_name(const mx_ctx *ctx, int q);
 
 /* ---------------------------------------------------------------------------
  * Learned demag surrogate (the paper's ML module, Sec. II-D: a network trained

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "MX_OK", 1: "MX_ERR_INVALID_ARG", 2: "MX_ERR_CUDA", 3: "MX_ER
 MX_TERM_DEMAG, MX_TERM_EXCH, MX_TERM_ANIS, MX_TERM_DMI, MX_TERM_ZEEMAN = 1, 2, 4, 8, 16
 MX_TERM_ALL = 31
 MX_RK4, MX_EULER, MX_MRI = 0, 1, 2
-MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE = 0, 1, 2
+MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE, MX_DEMAG_PLANE_PAIR = 0, 1, 2, 3
 MX_FFT_FP32, MX_FFT_SPLIT_BF16 = 0, 1
 
 
@@ -64,7 +64,8 @@ SIGNATURES = {
     "mx_demag_spectrum": (_I, [_P, _P, _P]),
     "mx_profile_step": (_I, [_P, _P, _I, _D, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_I), _I,
                              ctypes.POINTER(_I)]),
-    "mx_kernel_name": (ctypes.c_char_p, [_I]),
+    "mx_kernel_slot": (ctypes.c_char_p, [_I]),
+    "mx_kernel_name": (ctypes.c_char_p, [_P, _I]),
     "mx_energy_noalloc": (_I, [ctypes.POINTER(mx_params), _P, _P, _P, _P, _P, _P, _P]),
     "mx_cnn_num_params": (_I, []),
     "mx_cnn_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I]),
@@ -207,7 +208,19 @@ def mx_profile_step(ctx, m, nsteps, dt, method=MX_RK4, stream=None, max_kernels=
     n = _I()
     check(lib().mx_profile_step(ctx, ptr(m), int(nsteps), float(dt), int(method), stream_handle(stream),
                                 ms, cnt, max_kernels, ctypes.byref(n)))
-    return {lib().mx_kernel_name(q).decode(): (ms[q], cnt[q]) for q in range(n.value) if cnt[q] > 0}
+    return {lib().mx_kernel_slot(q).decode(): (ms[q], cnt[q]) for q in range(n.value) if cnt[q] > 0}
+
+
+def mx_kernel_names(ctx, max_kernels=32):
+    """{slot: kernel this context launches in it} for every timing slot."""
+    out, q = {}, 0
+    while q < max_kernels:
+        slot = lib().mx_kernel_slot(q).decode()
+        if not slot:
+            break
+        out[slot] = lib().mx_kernel_name(ctx, q).decode()
+        q += 1
+    return out
 
 
 def mx_adjoint_reserve(ctx, nsteps, checkpoint_every):

@@ -160,7 +160,32 @@ extern "C" {
 
 const char* mx_last_error(void) { return g_err.c_str(); }
 const char* mx_version(void) { return "libmx 0.1 (sm_103a)"; }
-const char* mx_kernel_name(int q) { return kernel_name(q); }
+const char* mx_kernel_slot(int q) { return kernel_name(q); }
+
+const char* mx_kernel_name(const mx_ctx* ctx, int q) {
+  if (!ctx || q < 0 || q >= KID_COUNT) return "";
+  const bool dft = ctx->p.fft_mode == MX_FFT_SPLIT_BF16;
+  switch (q) {
+    case KID_X_FWD:
+      if (ctx->plane) return dft ? "xfk_dft_kernel" : "xfk_kernel";
+      return ctx->fast_x ? "xf_kernel" : "x_fwd_kernel";
+    case KID_X_INV:
+      if (ctx->plane) return dft ? "xik_dft_kernel" : "xik_kernel";
+      return ctx->fast_x ? "xi_kernel" : "x_inv_kernel";
+    case KID_YZ:
+      if (ctx->plane) return ctx->quad ? "yzq_kernel" : "yzh_kernel";
+      return ctx->yz2d ? "yz2d_kernel" : "yz_fused_kernel";
+    case KID_Y_FWD: return "y_fwd_kernel";
+    case KID_Z_MUL: return "z_mul_kernel";
+    case KID_Y_INV: return "y_inv_kernel";
+    case KID_LOCAL: return "local_kernel";
+    case KID_NORMALIZE: return "normalize_kernel";
+    case KID_COPY: return "copy_kernel";
+    case KID_MRI_SLOW: return "mri_slow_kernel";
+    case KID_MRI_FAST: return "mri_fast_kernel";
+    default: return "";
+  }
+}
 
 mx_status mx_create(mx_ctx** out, const mx_params* p) {
   clear_error();
@@ -182,8 +207,8 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
     set_error("mx_create: need dx, dy, dz, Ms, gamma > 0 and A, alpha >= 0");
     return MX_ERR_INVALID_ARG;
   }
-  if (p->demag_path < MX_DEMAG_AUTO || p->demag_path > MX_DEMAG_PLANE) {
-    set_error("mx_create: demag_path must be MX_DEMAG_AUTO, MX_DEMAG_GENERIC or MX_DEMAG_PLANE");
+  if (p->demag_path < MX_DEMAG_AUTO || p->demag_path > MX_DEMAG_PLANE_PAIR) {
+    set_error("mx_create: demag_path must be MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE or MX_DEMAG_PLANE_PAIR");
     return MX_ERR_INVALID_ARG;
   }
   if (p->fft_mode != MX_FFT_FP32 && p->fft_mode != MX_FFT_SPLIT_BF16) {
@@ -209,6 +234,7 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
   g.Oy = g.Py / 2 + 1;
   g.Oz = g.Pz / 2 + 1;
   g.ncell = (long)g.nx * g.ny * g.nz;
+  g.oct4 = 0;
   const long nc = g.ncell;
   bool ok = true;
   auto alloc = [&](void** ptr, size_t bytes) {

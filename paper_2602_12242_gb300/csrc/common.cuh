@@ -79,17 +79,27 @@ struct Grid {
   int Hx;              // Px/2 + 1 (half spectrum along x); 1 when Px == 1
   int Oy, Oz;          // Py/2 + 1, Pz/2 + 1 (octant extents of the spectrum)
   long ncell;
+  int oct4;            // plane-path tensor octant split by qy mod 4 (else by qy mod 2)
 };
 
-// Tensor octant layout of the per-kx plane path: [kx][qz][qy mod 2][qy / 2][comp]
-// (6 comps innermost; qy split by parity so that the even-ky and odd-ky halves
-// of a plane each read contiguous rows, three float2 loads per (qz, qy)).
+// Tensor octant layouts of the per-kx plane path (6 comps innermost, so one
+// (qz, qy) is three float2 loads):
+//   oct4 == 0: [kx][qz][qy mod 2][qy / 2][comp], the even-ky and odd-ky halves
+//              of a plane (two-CTA plane kernel) each read contiguous rows;
+//   oct4 == 1: [kx][qz][qy mod 4][qy / 4][comp], Py/8 + 1 entries per class, so
+//              each CTA of the four-CTA plane kernel (one residue of ky mod 4)
+//              reads contiguous rows.
+__host__ __device__ __forceinline__ int plane_oct4_rows(const Grid& g) { return (g.Py >> 3) + 1; }
 __host__ __device__ __forceinline__ long plane_octant_index(const Grid& g, int kx, int comp, int qz, int qy) {
+  if (g.oct4) return ((((long)kx * g.Oz + qz) * 4 + (qy & 3)) * plane_oct4_rows(g) + (qy >> 2)) * 6 + comp;
   const int oyh = (g.Oy + 1) >> 1;
   return ((((long)kx * g.Oz + qz) * 2 + (qy & 1)) * oyh + (qy >> 1)) * 6 + comp;
 }
+// floats to allocate for either layout
 __host__ __device__ __forceinline__ long plane_octant_size(const Grid& g) {
-  return (long)g.Hx * g.Oz * 2 * ((g.Oy + 1) >> 1) * 6;
+  const long two = (long)g.Hx * g.Oz * 2 * ((g.Oy + 1) >> 1) * 6;
+  const long four = (long)g.Hx * g.Oz * 4 * plane_oct4_rows(g) * 6;
+  return two > four ? two : four;
 }
 
 struct LocalCoef {
@@ -141,6 +151,7 @@ struct mx_ctx {
   float2* tw_mk = nullptr;        // W_M^(s k) at [k * S + s] for the plane path's x line FFTs (M = E S)
   float2* tw_yh = nullptr;        // W_{Py/2}^k, k < Py/2
   bool plane = false;             // per-kx plane kernel (kx-major spectra and tensor)
+  bool quad = false;              // plane path uses the four-CTA y/z kernel (else the two-CTA one)
   void* dft_a = nullptr;          // split-BF16 DFT matrices (MX_FFT_SPLIT_BF16)
   int yz_tile = 1;                // kx columns per block in the fused kernel
   double* t_real = nullptr;       // FP64 real-space tensor octant (kept for checking)

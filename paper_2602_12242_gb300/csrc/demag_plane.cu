@@ -28,6 +28,7 @@
 #include "fft.cuh"
 #include "kernels.cuh"
 #include "bulk.cuh"
+#include "cluster.cuh"
 #include "regfft.cuh"
 
 namespace mx {
@@ -59,45 +60,82 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xfk_kernel(con
   const int z = blockIdx.x / ychunks;
   const int y0 = (blockIdx.x % ychunks) * kRows;
   const int tid = threadIdx.x;
-  for (int e = tid; e < kRows * M; e += NT) {
-    const int r = e / M, n = e % M;
+  // Ms m of rows y0 .. y0 + kRows - 1 as packed pairs z[n] = M[2n] + i M[2n+1];
+  // nx <= M, so only n < M/2 can be non-zero.  Every load of the thread is
+  // issued before the first is used.
+  constexpr int HALF = M / 2;
+  constexpr int NLD = (kRows * HALF + NT - 1) / NT;
+  float4 va[NLD], vb[NLD];
+#pragma unroll
+  for (int j = 0; j < NLD; ++j) {
+    const int e = tid + j * NT;
+    const int r = e / HALF, n = e % HALF;
     const int y = y0 + r;
-    float2 zx = make_float2(0.f, 0.f), zy = zx, zz = zx;
-    if (y < g.ny) {
-      const long cell = ((long)z * g.ny + y) * g.nx;
-      const int i0 = 2 * n, i1 = i0 + 1;
-      if (i0 < g.nx) {
-        const float4 a = __ldg(&m[cell + i0]);
-        const float s = ms_map ? __ldg(&ms_map[cell + i0]) : ms;
-        zx.x = s * a.x; zy.x = s * a.y; zz.x = s * a.z;
-      }
-      if (i1 < g.nx) {
-        const float4 b = __ldg(&m[cell + i1]);
-        const float s = ms_map ? __ldg(&ms_map[cell + i1]) : ms;
-        zx.y = s * b.x; zy.y = s * b.y; zz.y = s * b.z;
-      }
-    }
-    sm[(3 * r + 0) * P + n] = zx;
-    sm[(3 * r + 1) * P + n] = zy;
-    sm[(3 * r + 2) * P + n] = zz;
+    const bool in = e < kRows * HALF && y < g.ny;
+    const long cell = ((long)z * g.ny + (in ? y : 0)) * g.nx + 2 * n;
+    va[j] = (in && 2 * n < g.nx) ? __ldg(&m[cell]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    vb[j] = (in && 2 * n + 1 < g.nx) ? __ldg(&m[cell + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  float sa[NLD], sb[NLD];
+#pragma unroll
+  for (int j = 0; j < NLD; ++j) sa[j] = sb[j] = ms;
+  if (ms_map) {
+#pragma unroll
+    for (int j = 0; j < NLD; ++j) {
+      const int e = tid + j * NT;
+      const int r = e / HALF, n = e % HALF;
+      const int y = y0 + r;
+      const bool in = e < kRows * HALF && y < g.ny;
+      const long cell = ((long)z * g.ny + (in ? y : 0)) * g.nx + 2 * n;
+      if (in && 2 * n < g.nx) sa[j] = __ldg(&ms_map[cell]);
+      if (in && 2 * n + 1 < g.nx) sb[j] = __ldg(&ms_map[cell + 1]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NLD; ++j) {
+    const int e = tid + j * NT;
+    if (e >= kRows * HALF) break;
+    const int r = e / HALF, n = e % HALF;
+    sm[(3 * r + 0) * P + n] = make_float2(sa[j] * va[j].x, sb[j] * vb[j].x);
+    sm[(3 * r + 1) * P + n] = make_float2(sa[j] * va[j].y, sb[j] * vb[j].y);
+    sm[(3 * r + 2) * P + n] = make_float2(sa[j] * va[j].z, sb[j] * vb[j].z);
+  }
+  for (int e = tid; e < 3 * kRows * HALF; e += NT) sm[(e / HALF) * P + HALF + e % HALF] = make_float2(0.f, 0.f);
   __syncthreads();
   line_fft<E, S, false, false, true>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
-  const long plane = 3L * g.nz * g.ny;  // one kx
-  for (int e = tid; e < 3 * kRows * (M + 1); e += NT) {
-    const int r = e % kRows;
-    const int c = (e / kRows) % 3;
-    const int k = e / (3 * kRows);
-    const int y = y0 + r;
-    if (y >= g.ny) continue;
+  // r2c output from the packed transform Z: pairs (k, M - k), 0 < k < M/2,
+  // with E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i and
+  // T = W_2M^k O give X[k] = E + T and X[M-k] = conj(E - T); k = 0 gives
+  // X[0] = Re Z[0] + Im Z[0] and X[M] = Re Z[0] - Im Z[0]; X[M/2] = conj Z[M/2].
+  // Each thread keeps one line (row r fastest, so eight lanes store 64
+  // contiguous bytes of the kx-major spectrum).
+  constexpr int NL = 3 * kRows;
+  static_assert(NT % NL == 0, "xfk thread count");
+  const int li = tid % NL;
+  const int r = li % kRows, c = li / kRows;
+  const int y = y0 + r;
+  if (y < g.ny) {
+    const long plane = 3L * g.nz * g.ny;  // one kx
     const float2* L = sm + (3 * r + c) * P;
-    const float2 zk = L[k == M ? 0 : k];
-    const float2 zc = cconj(L[k == 0 ? 0 : M - k]);
-    const float2 Ev = cscale(cadd(zk, zc), 0.5f);
-    const float2 D = csub(zk, zc);
-    const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-    w1[(long)k * plane + ((long)c * g.nz + z) * g.ny + y] = cadd(Ev, cmul(__ldg(&twP[k]), O));
+    float2* dst = w1 + ((long)c * g.nz + z) * g.ny + y;
+#pragma unroll 4
+    for (int k = tid / NL; k <= M / 2; k += NT / NL) {
+      const float2 a = L[k];
+      if (k == 0) {
+        dst[0] = make_float2(a.x + a.y, 0.f);
+        dst[(long)M * plane] = make_float2(a.x - a.y, 0.f);
+      } else if (k == M / 2) {
+        dst[(long)k * plane] = cconj(a);
+      } else {
+        const float2 b = L[M - k];
+        const float2 Ev = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        const float2 O = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
+        const float2 T = cmul(__ldg(&twP[k]), O);
+        dst[(long)k * plane] = cadd(Ev, T);
+        dst[(long)(M - k) * plane] = cconj(csub(Ev, T));
+      }
+    }
   }
 }
 
@@ -116,47 +154,61 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(con
   const int z = blockIdx.x / ychunks;
   const int y0 = (blockIdx.x % ychunks) * kRows;
   const int tid = threadIdx.x;
-  const long plane = 3L * g.nz * g.ny;
-  constexpr int kB = 4;  // independent loads in flight per thread
-  for (int e0 = tid; e0 < 3 * kRows * M; e0 += NT * kB) {
-    float2 A[kB], Bv[kB];
+  // c2r input from the half spectrum X: pairs (k, M - k) with S = X[k] +
+  // conj X[M-k] and t = conj(W_2M^k) (X[k] - conj X[M-k]) give
+  // Z[k] = S + i t and Z[M-k] = conj(S - i t); k = 0 gives Z[0] (from X[0]
+  // and X[M]) and k = M/2 gives Z[M/2] = 2 conj X[M/2].  One line per
+  // thread, row r fastest (eight lanes load 64 contiguous bytes).
+  constexpr int NL = 3 * kRows;
+  static_assert(NT % NL == 0, "xik thread count");
+  {
+    const long plane = 3L * g.nz * g.ny;  // one kx
+    const int li = tid % NL;
+    const int r = li % kRows, c = li / kRows;
+    const int y = y0 + r;
+    float2* L = sm + (3 * r + c) * P;
+    const float2* src = w2 + ((long)c * g.nz + z) * g.ny + (y < g.ny ? y : 0);
+    // k = k0 + (NT / NL) j <= M/2, in batches of kB pairs with every load in flight
+    constexpr int KS = NT / NL;
+    constexpr int J = M / 2 / KS + 1;
+    constexpr int kB = 8;
+    const int k0 = tid / NL;
 #pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = e0 + u * NT;
-      const int r = e % kRows, c = (e / kRows) % 3, k = e / (3 * kRows);
-      const int y = y0 + r;
-      A[u] = Bv[u] = make_float2(0.f, 0.f);
-      if (e < 3 * kRows * M && y < g.ny) {
-        const long o = ((long)c * g.nz + z) * g.ny + y;
-        A[u] = __ldg(&w2[(long)k * plane + o]);
-        Bv[u] = __ldg(&w2[(long)(M - k) * plane + o]);
+    for (int j0 = 0; j0 < J; j0 += kB) {
+      float2 a[kB], b[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int k = k0 + KS * (j0 + u);
+        a[u] = b[u] = make_float2(0.f, 0.f);
+        if (j0 + u < J && k <= M / 2 && y < g.ny) {
+          a[u] = __ldg(&src[(long)k * plane]);
+          b[u] = cconj(__ldg(&src[(long)(M - k) * plane]));
+        }
       }
-    }
 #pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = e0 + u * NT;
-      if (e >= 3 * kRows * M) break;
-      const int r = e % kRows, c = (e / kRows) % 3, k = e / (3 * kRows);
-      const float2 a = A[u], b = cconj(Bv[u]);
-      const float2 Sv = cadd(a, b);
-      const float2 t = cmul(cconj(__ldg(&twP[k])), csub(a, b));
-      sm[(3 * r + c) * P + k] = make_float2(Sv.x - t.y, Sv.y + t.x);
+      for (int u = 0; u < kB; ++u) {
+        const int k = k0 + KS * (j0 + u);
+        if (j0 + u >= J || k > M / 2) break;
+        const float2 Sv = cadd(a[u], b[u]);
+        const float2 t = cmul(cconj(__ldg(&twP[k])), csub(a[u], b[u]));
+        L[k] = make_float2(Sv.x - t.y, Sv.y + t.x);
+        if (k > 0 && k < M / 2) L[M - k] = make_float2(Sv.x + t.y, t.x - Sv.y);
+      }
     }
   }
   __syncthreads();
   line_fft<E, S, true, false, true>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
-  for (int e = tid; e < kRows * g.nx; e += NT) {
-    const int r = e / g.nx, i = e % g.nx;
-    const int y = y0 + r;
-    if (y >= g.ny) continue;
+  // cells 2n and 2n + 1 of row r are the real and imaginary parts of element n
+  for (int e = tid; e < kRows * (M / 2); e += NT) {
+    const int r = e / (M / 2), n = e % (M / 2);
+    const int y = y0 + r, i = 2 * n;
+    if (y >= g.ny || i >= g.nx) continue;
     const float2* L = sm + (3 * r) * P;
-    const int n = i >> 1;
-    const bool odd = i & 1;
-    const float hx = odd ? L[n].y : L[n].x;
-    const float hy = odd ? L[P + n].y : L[P + n].x;
-    const float hz = odd ? L[2 * P + n].y : L[2 * P + n].x;
-    hd[((long)z * g.ny + y) * g.nx + i] = make_float4(hx, hy, hz, 0.f);
+    const float2 hx = L[n], hy = L[P + n], hz = L[2 * P + n];
+    float4* row = hd + ((long)z * g.ny + y) * g.nx;
+    row[i] = make_float4(hx.x, hy.x, hz.x, 0.f);
+    if (i + 1 < g.nx) row[i + 1] = make_float4(hx.y, hy.y, hz.y, 0.f);
   }
 }
 
@@ -170,21 +222,6 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(con
 // the conjugate twiddle), formed through distributed shared memory: CTA h
 // finishes lines [h L0, ...) of the plane with the other CTA's rows.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// generic address of the same shared-memory location in CTA `rank` of the cluster
-template <typename T> __device__ __forceinline__ const T* cluster_map(const T* p, unsigned rank) {
-  uint64_t out;
-  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"(p), "r"(rank));
-  return reinterpret_cast<const T*>(out);
-}
-
 template <int E, int S, int P>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
     yzh_kernel(const float2* __restrict__ w1, float2* __restrict__ w2, Grid g, const float* __restrict__ nhk,
@@ -496,11 +533,15 @@ static mx_status yzh_pass(mx_ctx* ctx, cudaStream_t st, bool setup) {
 mx_status plane_setup(mx_ctx* ctx) {
   MX_TRY(upload_w32());
   const int path = ctx->p.demag_path;
-  ctx->plane = path != MX_DEMAG_GENERIC && !ctx->fused_yz &&
-               xk_pass(ctx, nullptr, nullptr, false, nullptr, true) == MX_OK &&
-               yzh_pass(ctx, nullptr, true) == MX_OK;
+  const bool xk = path != MX_DEMAG_GENERIC && !ctx->fused_yz &&
+                  xk_pass(ctx, nullptr, nullptr, false, nullptr, true) == MX_OK;
+  // the four-CTA y/z kernel where it fits, else the two-CTA one
+  // (MX_DEMAG_PLANE_PAIR forces the two-CTA kernel)
+  ctx->quad = xk && path != MX_DEMAG_PLANE_PAIR && quad_pass(ctx, nullptr, true) == MX_OK;
+  ctx->plane = ctx->quad || (xk && yzh_pass(ctx, nullptr, true) == MX_OK);
+  ctx->g.oct4 = ctx->quad ? 1 : 0;
   clear_error();
-  if (path == MX_DEMAG_PLANE && !ctx->plane) {
+  if ((path == MX_DEMAG_PLANE || path == MX_DEMAG_PLANE_PAIR) && !ctx->plane) {
     set_error("mx_create: the per-kx plane demag kernel does not support this grid");
     return MX_ERR_UNSUPPORTED;
   }
@@ -523,7 +564,7 @@ mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
   }
   {
     ProfScope ps(ctx, KID_YZ, st);
-    MX_TRY(yzh_pass(ctx, st, false));
+    MX_TRY(ctx->quad ? quad_pass(ctx, st, false) : yzh_pass(ctx, st, false));
   }
   {
     ProfScope ps(ctx, KID_X_INV, st);

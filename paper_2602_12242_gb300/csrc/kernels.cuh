@@ -47,6 +47,10 @@ mx_status plane_setup(mx_ctx* ctx);
 mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st);
 mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 
+// demag_quad.cu: the four-CTA y/z plane kernel (setup: check the grid fits and
+// set its attributes; otherwise launch it on w1 -> w2)
+mx_status quad_pass(mx_ctx* ctx, cudaStream_t st, bool setup);
+
 // cnn.cu
 mx_status cnn_demag(struct mx_cnn* n, const float4* m, float4* h, cudaStream_t st);
 bool cnn_matches(const struct mx_cnn* n, const Grid& g);

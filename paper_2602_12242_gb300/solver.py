@@ -192,6 +192,17 @@ class Context:
         torch.cuda.current_stream().synchronize()
         return out
 
+    def kernel_names(self):
+        """{timing slot: the kernel this context launches in it}."""
+        return L.mx_kernel_names(self.h)
+
+    def kernel_name(self, slot):
+        """The kernel launched in timing slot `slot` (an index or a slot name)."""
+        names = self.kernel_names()
+        if isinstance(slot, int):
+            slot = list(names)[slot]
+        return names[slot]
+
     def profile_step(self, m, nsteps, dt, method="rk4", stream=None):
         self._check(m)
         return L.mx_profile_step(self.h, m, nsteps, dt, _METHODS[method], stream)

@@ -30,28 +30,43 @@ def test_film_spectrum_has_four_tensor_components():
     assert b["yz_fused"] == 2 * (3 * 128 * 513 * 8) + 4 * 1 * 129 * 513 * 4
 
 
-def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
-    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    entry = t["bulk"]["yz_fused"]
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch, tmp_path):
+    entry = {"dram_bytes_per_launch": 123456, "source_digest": "ab" * 8}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"bulk": {"yzq_kernel": entry}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "source_digest", lambda kernel=None: entry["source_digest"])
-    assert bench.load_traffic("bulk", "yz_fused") == entry["dram_bytes_per_launch"]
+    assert bench.load_traffic("bulk", "yzq_kernel") == entry["dram_bytes_per_launch"]
     monkeypatch.setattr(bench, "source_digest", lambda kernel=None: "0" * 16)
-    assert bench.load_traffic("bulk", "yz_fused") is None
+    assert bench.load_traffic("bulk", "yzq_kernel") is None
+
+
+def test_committed_traffic_entries_name_known_kernels():
+    t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for wl, entries in t.items():
+        if wl.startswith("_"):
+            continue
+        for kernel, e in entries.items():
+            assert kernel in bench.KERNEL_TU and e["dram_bytes_per_launch"] > 0
 
 
 def test_kernel_digests_cover_their_translation_unit_and_headers_only():
     """A kernel's digest covers the file that defines it and every local
     header it includes (through other headers too), and nothing else."""
-    plane = bench.kernel_sources("yz_fused")
+    plane = bench.kernel_sources("yzh_kernel")
     for f in ("paper_2602_12242_gb300/csrc/demag_plane.cu", "paper_2602_12242_gb300/csrc/regfft.cuh",
               "paper_2602_12242_gb300/csrc/fft.cuh", "paper_2602_12242_gb300/csrc/bulk.cuh",
-              "paper_2602_12242_gb300/csrc/common.cuh", "include/mx.h"):
+              "paper_2602_12242_gb300/csrc/cluster.cuh", "paper_2602_12242_gb300/csrc/common.cuh", "include/mx.h"):
         assert f in plane
-    assert not any(f.endswith(("fno.cu", "cnn.cu", "api.cu", "local.cu")) for f in plane)
-    local = bench.kernel_sources("local_stage_rk4_s1")
+    assert not any(f.endswith(("fno.cu", "cnn.cu", "api.cu", "local.cu", "demag_quad.cu")) for f in plane)
+    quad = bench.kernel_sources("yzq_kernel")
+    assert "paper_2602_12242_gb300/csrc/demag_quad.cu" in quad
+    assert not any(f.endswith(("demag_plane.cu", "bulk.cuh")) for f in quad)
+    local = bench.kernel_sources("local_kernel")
     assert "paper_2602_12242_gb300/csrc/local.cuh" in local
     assert not any(f.endswith("demag_plane.cu") for f in local)
-    assert bench.source_digest("x_fwd") == bench.source_digest("yz_fused") != bench.source_digest("local_stage_rk4_s1")
+    assert bench.source_digest("xfk_kernel") == bench.source_digest("yzh_kernel") != bench.source_digest("local_kernel")
+    assert bench.source_digest("yzq_kernel") != bench.source_digest("yzh_kernel")
 
 
 def test_kernel_digest_ignores_comments_and_layout(tmp_path):

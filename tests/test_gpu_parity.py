@@ -32,6 +32,10 @@ CASES = {
     # planes too large for the fused y/z kernel: separate y, z (+multiply), y passes
     "tall64x512x16": cfg_of(nx=64, ny=512, nz=16),
     "mid40x300x3": cfg_of(nx=40, ny=300, nz=3, dx=2.5e-9, dy=2e-9, dz=3e-9, D=1e-3, dmi=True),
+    # four-CTA plane kernel: Py/4 = 64, 128, 512 with Pz = 16, 32 (nz < Pz/2), 4
+    "quad70x100x6": cfg_of(nx=70, ny=100, nz=6),
+    "quad50x200x9": cfg_of(nx=50, ny=200, nz=9, dx=2.5e-9, dy=2e-9, dz=3e-9, D=1e-3, dmi=True),
+    "quad33x600x2": cfg_of(nx=33, ny=600, nz=2),
     # Px/2 = 1024: the widest x transforms (32 threads per line)
     "wide600x24x2": cfg_of(nx=600, ny=24, nz=2),
     # one z plane, Py/2 = 64, 256, 512 (single-z-plane y kernel sizes)
@@ -40,7 +44,7 @@ CASES = {
     "sheet24x300x1": cfg_of(nx=24, ny=300, nz=1, dx=3.9e-9, dy=3.9e-9, dz=3e-9),
 }
 SMALL = [k for k in CASES if k not in ("tall64x512x16", "wide600x24x2", "sheet30x40x1", "sheet40x200x1",
-                                       "sheet24x300x1")]
+                                       "sheet24x300x1", "quad70x100x6", "quad50x200x9", "quad33x600x2")]
 
 
 def f32(a):
@@ -303,20 +307,29 @@ def test_bulk_workload_full_size_sampled_direct_sum():
 
 
 @pytest.mark.parametrize("name", ["tall64x512x16", "mid40x300x3", "wide600x24x2", "ragged37x21x5", "film17x9", "cell1",
-                                  "sheet30x40x1", "sheet40x200x1", "sheet24x300x1"])
-@pytest.mark.parametrize("path", ["generic", "plane", "auto"])
+                                  "sheet30x40x1", "sheet40x200x1", "sheet24x300x1", "quad70x100x6", "quad50x200x9",
+                                  "quad33x600x2"])
+@pytest.mark.parametrize("path", ["generic", "plane", "plane_pair", "auto"])
 def test_each_demag_schedule_matches_oracle(name, path):
-    """Every schedule of the convolution (size-generic passes, per-kx plane kernel)
-    gives the oracle's field; grids the plane kernel cannot take are refused."""
+    """Every schedule of the convolution (size-generic passes, per-kx plane path
+    with the four-CTA or the two-CTA y/z kernel) gives the oracle's field;
+    grids the plane path cannot take are refused."""
     from paper_2602_12242_gb300 import MX_TERM_DEMAG, MxError, _lib
     c = CASES[name]
-    code = {"generic": _lib.MX_DEMAG_GENERIC, "plane": _lib.MX_DEMAG_PLANE, "auto": _lib.MX_DEMAG_AUTO}[path]
+    code = {"generic": _lib.MX_DEMAG_GENERIC, "plane": _lib.MX_DEMAG_PLANE, "plane_pair": _lib.MX_DEMAG_PLANE_PAIR,
+            "auto": _lib.MX_DEMAG_AUTO}[path]
     try:
         ctx = context(c, demag_path=code)
     except MxError as e:
-        assert path == "plane" and e.status == _lib.MX_ERR_UNSUPPORTED
+        assert path in ("plane", "plane_pair") and e.status == _lib.MX_ERR_UNSUPPORTED
         assert name in ("cell1", "film17x9") or c["nz"] == 1  # Py/2 < 16 or Pz < 4
         return
+    # Py/4 >= 64 and Pz >= 4 take the four-CTA kernel unless the two-CTA one is forced
+    Px, Py, Pz = ctx.padded_dims
+    if path == "plane":
+        assert ctx.kernel_name("yz_fused") == ("yzq_kernel" if Py >= 256 else "yzh_kernel")
+    if path == "plane_pair":
+        assert ctx.kernel_name("yz_fused") == "yzh_kernel"
     m = f32(random_m(c, 19))
     h = host(ctx.heff(gpu_m(m), terms=MX_TERM_DEMAG))
     ref = mm.demag_field(problem(c), t64(m)).numpy()
