@@ -345,6 +345,7 @@ def rk4_step(p, m0, dt, f=None):
 
 
 def euler_step(p, m0, dt, f=None):
+    """One forward Euler step, m1 = normalize(m0 + dt f(m0)) (Sec. II-D, III-E)."""
     f = f or (lambda x: rhs(p, x))
     return normalize(m0 + dt * f(m0))
 

@@ -137,13 +137,13 @@ def test_llg_orthogonality_and_fixed_point():
     assert float(mm.llg_rhs(p, m, 3.7e4 * m).abs().max()) < 1e-6
 
 
-def _macrospin(alpha, dt, nsteps, H=1e5, precession=True):
+def _macrospin(alpha, dt, nsteps, H=1e5, precession=True, method="rk4"):
     p = mm.Problem(1, 1, 1, 2e-9, 2e-9, 2e-9, Ms=8e5, A=0.0, alpha=alpha, h_bias=(0, 0, H), demag=False,
                    precession=precession)
     th0, ph0 = 2.0, 0.3
     m = torch.tensor([[[[math.sin(th0) * math.cos(ph0), math.sin(th0) * math.sin(ph0), math.cos(th0)]]]],
                      dtype=torch.float64)
-    mt = mm.run(p, m, dt, nsteps)
+    mt = mm.run(p, m, dt, nsteps, method=method)
     t = dt * nsteps
     c = p.gamma * H / (1 + alpha ** 2)
     th = 2 * math.atan(math.tan(th0 / 2) * math.exp(-alpha * c * t))
@@ -165,6 +165,22 @@ def test_macrospin_closed_form_and_rk4_order():
     m = mm.normalize(torch.tensor([[[[0.6, 0.1, -0.5]]]], dtype=torch.float64))
     Hd = mm.demag_field(p, m)
     assert torch.allclose(Hd, -8e5 / 3 * m, rtol=1e-12)
+
+
+def test_macrospin_forward_euler_is_first_order_with_unit_norm():
+    """Forward Euler with renormalisation (Sec. II-D, III-E) converges to the
+    same closed form at first order: halving dt halves the error at a fixed
+    time; every step leaves |m| = 1."""
+    T = 2e-11
+    e1 = _macrospin(0.1, T / 400, 400, method="euler")
+    e2 = _macrospin(0.1, T / 800, 800, method="euler")
+    assert e1 < 5e-2
+    assert 1.8 < e1 / e2 < 2.2
+    p = mm.Problem(6, 5, 2, 2e-9, 2e-9, 2e-9, Ms=8e5, A=1.3e-11, Ku=5e3, alpha=0.5, h_bias=(0, 0, 1e4))
+    m = rand_m(p.shape, 31)
+    for _ in range(5):
+        m = mm.euler_step(p, m, 1e-13)
+        assert float((m.norm(dim=-1) - 1).abs().max()) < 1e-15
 
 
 def test_macrospin_without_precession_relaxes_in_its_plane():

@@ -261,6 +261,17 @@ def test_rk4_without_renormalisation_is_caught(monkeypatch):
     planted_fails(pins_fields.test_energy_decays_and_norm_conserved_plain)
 
 
+def test_euler_without_renormalisation_is_caught(monkeypatch):
+    monkeypatch.setattr(mm, "euler_step", lambda p, m0, dt, f=None: m0 + dt * (f or (lambda x: mm.rhs(p, x)))(m0))
+    planted_fails(pins_fields.test_macrospin_forward_euler_is_first_order_with_unit_norm)
+
+
+def test_euler_with_half_the_step_is_caught(monkeypatch):
+    orig = mm.euler_step
+    monkeypatch.setattr(mm, "euler_step", lambda p, m0, dt, f=None: orig(p, m0, 0.5 * dt, f))
+    planted_fails(pins_fields.test_macrospin_forward_euler_is_first_order_with_unit_norm)
+
+
 def test_normalisation_by_the_squared_norm_is_caught(monkeypatch):
     monkeypatch.setattr(mm, "normalize", lambda m: m / (m * m).sum(-1, keepdim=True))
     planted_fails(pins_fields.test_energy_decays_and_norm_conserved_plain)
