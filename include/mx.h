@@ -226,7 +226,10 @@ mx_status mx_exchange_energy_central(mx_ctx *ctx, const float *m, double *e_out,
  *   axis_map DEVICE float4 unit axes or NULL (p->ku_axis)
  *   e_out    DEVICE array of 5 doubles: demag, exchange, anisotropy, DMI,
  *            Zeeman, as in mx_energy
- * Limit: nx*ny*nz <= 4,194,304 cells; larger grids return MX_ERR_UNSUPPORTED.
+ * Limit: 1..2048 cells per axis and nx*ny*nz <= 4,194,304 cells; larger
+ * grids return MX_ERR_UNSUPPORTED before any device call.  NULL m or e_out,
+ * or a misaligned pointer (m, h_demag, axis_map 16 bytes; ms_map, ku_map 4;
+ * e_out 8), returns MX_ERR_INVALID_ARG before any device call.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  Enqueued on `stream`, no synchronisation.
@@ -242,6 +245,17 @@ mx_status mx_energy_noalloc(const mx_params *p, const float *m, const float *h_d
  * MX_ERR_TIMEOUT if a bounded wait (bulk copy of the demag kernel, tensor
  * cores of an attached surrogate) ran out (results are then invalid). */
 mx_status mx_sync(mx_ctx *ctx, mx_stream_t stream);
+
+/* Failure-detection test hook (no counterpart in the paper).  on != 0: every
+ * later demag evaluation of this context arms the two-CTA plane kernel's
+ * bulk-copy barrier for the plane's bytes but issues no copy, so the barrier
+ * never completes; the kernel's bounded wait gives up after about one
+ * second, the kernel runs to its end on stale shared memory (the demag field
+ * is then invalid) and the next mx_sync returns MX_ERR_TIMEOUT.  No copy is
+ * in flight at any time.  on == 0 restores normal operation; the context
+ * stays usable.  MX_ERR_UNSUPPORTED unless the context runs the two-CTA
+ * kernel with bulk copies (demag_path MX_DEMAG_PLANE_PAIR, even ny). */
+mx_status mx_inject_wait_timeout(mx_ctx *ctx, int on);
 
 /* Padded grid of this context: out[0..2] = Px, Py, Pz. */
 mx_status mx_padded_dims(const mx_ctx *ctx, int out[3]);

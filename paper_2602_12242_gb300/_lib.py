@@ -65,6 +65,7 @@ SIGNATURES = {
     "mx_profile_step": (_I, [_P, _P, _I, _D, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_I), _I,
                              ctypes.POINTER(_I)]),
     "mx_kernel_slot": (ctypes.c_char_p, [_I]),
+    "mx_inject_wait_timeout": (_I, [_P, _I]),
     "mx_kernel_name": (ctypes.c_char_p, [_P, _I]),
     "mx_energy_noalloc": (_I, [ctypes.POINTER(mx_params), _P, _P, _P, _P, _P, _P, _P]),
     "mx_cnn_num_params": (_I, []),
@@ -209,6 +210,10 @@ def mx_profile_step(ctx, m, nsteps, dt, method=MX_RK4, stream=None, max_kernels=
     check(lib().mx_profile_step(ctx, ptr(m), int(nsteps), float(dt), int(method), stream_handle(stream),
                                 ms, cnt, max_kernels, ctypes.byref(n)))
     return {lib().mx_kernel_slot(q).decode(): (ms[q], cnt[q]) for q in range(n.value) if cnt[q] > 0}
+
+
+def mx_inject_wait_timeout(ctx, on):
+    check(lib().mx_inject_wait_timeout(ctx, int(bool(on))))
 
 
 def mx_kernel_names(ctx, max_kernels=32):

@@ -305,6 +305,17 @@ mx_status mx_destroy(mx_ctx* ctx) {
   return MX_OK;
 }
 
+mx_status mx_inject_wait_timeout(mx_ctx* ctx, int on) {
+  MX_TRY(check_ctx(ctx));
+  if (on && !(ctx->plane && !ctx->quad && (ctx->g.ny & 1) == 0 && !ctx->surrogate && !ctx->fno)) {
+    set_error("mx_inject_wait_timeout: needs the two-CTA plane kernel with bulk copies (MX_DEMAG_PLANE_PAIR, even ny)");
+    return MX_ERR_UNSUPPORTED;
+  }
+  invalidate_graph(ctx);
+  ctx->inject_wait_timeout = on != 0;
+  return MX_OK;
+}
+
 mx_status mx_padded_dims(const mx_ctx* ctx, int out[3]) {
   MX_TRY(check_ctx(ctx));
   if (!out) {

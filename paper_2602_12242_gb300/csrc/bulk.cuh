@@ -14,7 +14,8 @@
 
 namespace mx {
 
-constexpr int kBulkWaitLimit = 1 << 22;  // try_wait polls before a wait gives up
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;  // a wait gives up after about one second
+constexpr int kBulkWaitPolls = 1 << 26;                        // and after this many polls in any case
 
 __device__ __forceinline__ uint32_t smem_u32addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -63,10 +64,19 @@ __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Bounded wait for the completion of phase `parity` of `bar`.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the completion of phase `parity` of `bar`: false after
+// about kBulkWaitNs of global time (checked every 256 polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32addr(bar);
-  for (int i = 0; i < kBulkWaitLimit; ++i) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kBulkWaitPolls; ++i) {
+    if ((i & 255) == 255 && global_ns() - t0 > kBulkWaitNs) return false;
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

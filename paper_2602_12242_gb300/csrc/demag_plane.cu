@@ -226,7 +226,7 @@ template <int E, int S, int P>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
     yzh_kernel(const float2* __restrict__ w1, float2* __restrict__ w2, Grid g, const float* __restrict__ nhk,
                const float2* __restrict__ twPy, const float2* __restrict__ twH, const float2* __restrict__ twz,
-               int* flag) {
+               int* flag, int arm_only) {
   constexpr int LH = E * S;                       // Py / 2
   constexpr int PITCH = YzhPitch<E, S>::value;
   constexpr int Q = P / 4;                        // points per residue class of kz
@@ -263,8 +263,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPlaneNT, 1)
   if (bulk) {
     if (tid == 0) {
       mbar_arrive_expect_tx(&bar, (uint32_t)nlines * row_bytes);
-      for (int line = 0; line < nlines; ++line)
-        bulk_load(sm + line * PITCH, w1 + kxoff + (long)line * ny, row_bytes, &bar);
+      // arm_only (mx_inject_wait_timeout): the barrier expects the plane's
+      // bytes but no copy is issued, so it never completes, the bounded wait
+      // below runs out and sets kFlagTimeout, and no copy is ever in flight
+      if (!arm_only)
+        for (int line = 0; line < nlines; ++line)
+          bulk_load(sm + line * PITCH, w1 + kxoff + (long)line * ny, row_bytes, &bar);
     }
     for (int e = tid; e < nlines * (LH - ny); e += NT) {
       const int line = e / (LH - ny), y = ny + e % (LH - ny);
@@ -491,7 +495,7 @@ static mx_status yzh_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
     return MX_OK;
   }
   yzh_kernel<E, S, P><<<2 * g.Hx, kPlaneNT, sm, st>>>(ctx->w1, ctx->w2, g, ctx->nhat, ctx->tw_y, ctx->tw_yh, ctx->tw_z,
-                                                   ctx->flag);
+                                                   ctx->flag, ctx->inject_wait_timeout ? 1 : 0);
   return launch_check("yzh_kernel");
 }
 

@@ -50,3 +50,40 @@ def test_create_refuses(L, name, kw, status):
     assert got == getattr(L, status), (name, got, L.lib().mx_last_error())
     assert not h.value
     assert L.lib().mx_last_error()
+
+
+NOALLOC_CASES = [
+    ("axis far beyond 2048", dict(nx=1 << 22, ny=1 << 22, nz=1 << 22), {}, "MX_ERR_UNSUPPORTED"),
+    ("one axis over 2048", dict(nx=4096, ny=1, nz=1), {}, "MX_ERR_UNSUPPORTED"),
+    ("cells over the scratch limit", dict(nx=2048, ny=2048, nz=2), {}, "MX_ERR_UNSUPPORTED"),
+    ("empty grid", dict(nx=0), {}, "MX_ERR_UNSUPPORTED"),
+    ("zero Ms", dict(Ms=0.0), {}, "MX_ERR_INVALID_ARG"),
+    ("misaligned Ms map", {}, dict(ms_map=2), "MX_ERR_INVALID_ARG"),
+    ("misaligned Ku map", {}, dict(ku_map=1), "MX_ERR_INVALID_ARG"),
+    ("misaligned m", {}, dict(m=8), "MX_ERR_INVALID_ARG"),
+    ("NULL m", {}, dict(m=None), "MX_ERR_INVALID_ARG"),
+]
+
+
+@pytest.mark.parametrize("name,kw,ptrs,status", NOALLOC_CASES, ids=[c[0] for c in NOALLOC_CASES])
+def test_energy_noalloc_refuses_before_any_device_call(L, name, kw, ptrs, status):
+    """mx_energy_noalloc's checks use no device: host buffers stand in for the
+    device pointers (never dereferenced), offsets make them misaligned."""
+    buf = (ctypes.c_double * 64)()
+    base = ctypes.addressof(buf)
+    base += (-base) % 16
+
+    def at(off):
+        return ctypes.c_void_p(None if off is None else base + off)
+
+    args = dict(m=0, h_demag=None, ms_map=None, ku_map=None, axis_map=None)
+    args.update(ptrs)
+    p = params(L, **kw)
+    got = L.lib().mx_energy_noalloc(ctypes.byref(p), at(args["m"]), at(args["h_demag"]), at(args["ms_map"]),
+                                    at(args["ku_map"]), at(args["axis_map"]), at(256), ctypes.c_void_p(None))
+    assert got == getattr(L, status), (name, got, L.lib().mx_last_error())
+    assert L.lib().mx_last_error()
+
+
+def test_wait_timeout_hook_refuses_a_null_context(L):
+    assert L.lib().mx_inject_wait_timeout(ctypes.c_void_p(None), 1) == L.MX_ERR_INVALID_ARG
