@@ -91,6 +91,8 @@ struct StageIO {
   int terms;          // MX_TERM_* mask (LM_HEFF only)
 };
 LocalCoef local_coef(const mx_ctx* ctx);
+// the same coefficients from parameters and caller-owned maps (any may be null)
+LocalCoef local_coef_from(const mx_params& p, const float* ms_map, const float* ku_map, const float4* axis_map);
 mx_status local_stage(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st);
 mx_status normalize_field(mx_ctx* ctx, float4* m, cudaStream_t st);
 mx_status copy_field(mx_ctx* ctx, float4* dst, const float4* src, cudaStream_t st);

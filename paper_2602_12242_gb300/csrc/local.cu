@@ -88,8 +88,9 @@ __global__ void __launch_bounds__(256) energy_kernel(const float4* __restrict__ 
   }
 }
 
-LocalCoef local_coef(const mx_ctx* ctx) {
-  const mx_params& p = ctx->p;
+LocalCoef local_coef(const mx_ctx* ctx) { return local_coef_from(ctx->p, ctx->ms_map, ctx->ku_map, ctx->axis_map); }
+
+LocalCoef local_coef_from(const mx_params& p, const float* ms_map, const float* ku_map, const float4* axis_map) {
   LocalCoef c;
   c.inv_dx2 = (float)(1.0 / (p.dx * p.dx));
   c.inv_dy2 = (float)(1.0 / (p.dy * p.dy));
@@ -115,9 +116,9 @@ LocalCoef local_coef(const mx_ctx* ctx) {
   c.alpha = (float)p.alpha;
   c.dmi = dmi ? 1 : 0;
   c.precession = p.precession ? 1 : 0;
-  c.ms_map = ctx->ms_map;
-  c.ku_map = ctx->ku_map;
-  c.axis_map = ctx->axis_map;
+  c.ms_map = ms_map;
+  c.ku_map = ku_map;
+  c.axis_map = axis_map;
   return c;
 }
 

@@ -114,39 +114,6 @@ __global__ void __launch_bounds__(kNoallocThreads) energy_reduce_kernel(const do
   if (threadIdx.x < 5) e_out[threadIdx.x] = red[threadIdx.x][0];
 }
 
-static LocalCoef coef_from_params(const mx_params& p, const float* ms_map, const float* ku_map,
-                                  const float4* axis_map) {
-  LocalCoef c;
-  c.inv_dx2 = (float)(1.0 / (p.dx * p.dx));
-  c.inv_dy2 = (float)(1.0 / (p.dy * p.dy));
-  c.inv_dz2 = (float)(1.0 / (p.dz * p.dz));
-  c.inv_2dx = (float)(0.5 / p.dx);
-  c.inv_2dy = (float)(0.5 / p.dy);
-  const bool dmi = p.dmi_interfacial && p.D != 0.0 && p.A > 0.0;
-  const double kappa = dmi ? p.D / (2.0 * p.A) : 0.0;
-  c.kdx = (float)(p.dx * kappa);
-  c.kdy = (float)(p.dy * kappa);
-  c.cA = (float)(2.0 * p.A / kMu0);
-  c.cD = (float)(2.0 * p.D / kMu0);
-  c.cK = (float)(2.0 * p.Ku / kMu0);
-  c.Ms = (float)p.Ms;
-  double ax = p.ku_axis[0], ay = p.ku_axis[1], az = p.ku_axis[2];
-  const double an = sqrt(ax * ax + ay * ay + az * az);
-  if (an > 0) { ax /= an; ay /= an; az /= an; }
-  c.ax = (float)ax; c.ay = (float)ay; c.az = (float)az;
-  c.hx = (float)p.h_bias[0];
-  c.hy = (float)p.h_bias[1];
-  c.hz = (float)p.h_bias[2];
-  c.llg = (float)(-p.gamma / (1.0 + p.alpha * p.alpha));
-  c.alpha = (float)p.alpha;
-  c.dmi = dmi ? 1 : 0;
-  c.precession = p.precession ? 1 : 0;
-  c.ms_map = ms_map;
-  c.ku_map = ku_map;
-  c.axis_map = axis_map;
-  return c;
-}
-
 }  // namespace mx
 
 using namespace mx;
@@ -160,13 +127,18 @@ extern "C" mx_status mx_energy_noalloc(const mx_params* p, const float* m, const
     return MX_ERR_INVALID_ARG;
   }
   if ((((uintptr_t)m) & 15) || (h_demag && (((uintptr_t)h_demag) & 15)) || (axis_map && (((uintptr_t)axis_map) & 15)) ||
-      (((uintptr_t)e_out) & 7)) {
-    set_error("mx_energy_noalloc: m, h_demag and axis_map must be 16-byte aligned, e_out 8-byte aligned");
+      (ms_map && (((uintptr_t)ms_map) & 3)) || (ku_map && (((uintptr_t)ku_map) & 3)) || (((uintptr_t)e_out) & 7)) {
+    set_error("mx_energy_noalloc: m, h_demag and axis_map must be 16-byte aligned, ms_map and ku_map 4-byte, "
+              "e_out 8-byte aligned");
     return MX_ERR_INVALID_ARG;
   }
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || !(p->dx > 0 && p->dy > 0 && p->dz > 0) || !(p->Ms > 0) ||
-      !(p->A >= 0)) {
-    set_error("mx_energy_noalloc: need nx, ny, nz >= 1, dx, dy, dz, Ms > 0 and A >= 0");
+  // the same per-axis limit as mx_create, checked before the cell count is formed
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 2048 || p->ny > 2048 || p->nz > 2048) {
+    set_error("mx_energy_noalloc: grid must be 1..2048 cells per axis");
+    return MX_ERR_UNSUPPORTED;
+  }
+  if (!(p->dx > 0 && p->dy > 0 && p->dz > 0) || !(p->Ms > 0) || !(p->A >= 0)) {
+    set_error("mx_energy_noalloc: need dx, dy, dz, Ms > 0 and A >= 0");
     return MX_ERR_INVALID_ARG;
   }
   const long ncell = (long)p->nx * p->ny * p->nz;
@@ -182,7 +154,7 @@ extern "C" mx_status mx_energy_noalloc(const mx_params* p, const float* m, const
   g.ny = p->ny;
   g.nz = p->nz;
   g.ncell = ncell;
-  const LocalCoef c = coef_from_params(*p, ms_map, ku_map, (const float4*)axis_map);
+  const LocalCoef c = local_coef_from(*p, ms_map, ku_map, (const float4*)axis_map);
   const double V = p->dx * p->dy * p->dz;
   const int nblocks = (int)((ncell + kNoallocThreads - 1) / kNoallocThreads);
   cudaStream_t st = (cudaStream_t)stream;

@@ -58,6 +58,41 @@ def test_noalloc_energy_equals_mx_energy_twice(case):
             assert abs(got[k] - ref[k]) <= TOL_ENERGY * scale, (k, got[k], ref[k])
 
 
+def _noalloc_vs_energy(c, seed, with_demag=True):
+    """mx_energy_noalloc against mx_energy on one grid (uniform Ms and Ku, grain axes)."""
+    from paper_2602_12242_gb300 import MX_TERM_DEMAG, _lib, inputs
+    from paper_2602_12242_gb300.solver import to_dev4
+    shape = (c["nz"], c["ny"], c["nx"])
+    axis = inputs.grain_axes(shape, (16, 16, 4), seed).astype(np.float32)
+    ctx = context(c, axis=axis)
+    m = to_dev4(random_m(c, seed + 1))
+    ref = ctx.energy(m)
+    hd = ctx.heff(m, terms=MX_TERM_DEMAG) if with_demag else None
+    out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+    _lib.mx_energy_noalloc(_params(ctx), m, out, h_demag=hd, axis_map=to_dev4(axis))
+    torch.cuda.synchronize()
+    return dict(zip(("demag", "exch", "anis", "dmi", "zeeman"), out.cpu().tolist())), ref
+
+
+def test_noalloc_after_a_larger_grid_and_without_demag():
+    """A grid of more than 65,536 cells (512 blocks: the reduction's strided
+    loop takes several passes) between two calls on a small grid, which must
+    not see the larger call's leftover rows; then h_demag = NULL, whose demag
+    energy is exactly 0 while the other terms still match."""
+    small = cfg_of(nx=20, ny=12, nz=3, Ku=3e4, h_bias=(1e4, 0.0, -2e4))
+    large = cfg_of(nx=128, ny=128, nz=8, Ku=4e5)
+    for c, seed in ((small, 81), (large, 83), (small, 81)):
+        got, ref = _noalloc_vs_energy(c, seed)
+        scale = sum(abs(v) for v in ref.values())
+        for k in ref:
+            assert abs(got[k] - ref[k]) <= TOL_ENERGY * scale, (c["nx"], k, got[k], ref[k])
+    got, ref = _noalloc_vs_energy(small, 85, with_demag=False)
+    assert got["demag"] == 0.0
+    scale = sum(abs(v) for k, v in ref.items() if k != "demag")
+    for k in ("exch", "anis", "dmi", "zeeman"):
+        assert abs(got[k] - ref[k]) <= TOL_ENERGY * scale, (k, got[k], ref[k])
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
     from paper_2602_12242_gb300 import MxError, _lib
     p = _lib.mx_params()
