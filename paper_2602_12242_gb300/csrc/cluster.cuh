@@ -28,6 +28,16 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
+// Split form with memory ordering: this thread's earlier memory accesses
+// (shared memory of any CTA of the cluster included) are performed before the
+// arrive, and accesses after the wait see what the other threads released.
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // generic address of the same shared-memory location in CTA `rank` of the cluster
 template <typename T> __device__ __forceinline__ const T* cluster_map(const T* p, unsigned rank) {
   uint64_t out;

@@ -169,17 +169,69 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
   float2* twI = twF + L4;              // [k1 S + s]: W_Py^(k1 (4 s + h))
   float2* twA = twI + L4;              // [n]: W_Py^(h n S) = W_4E^(h n)
   float2* twB = twA + E;               // [k2]: W_Py^(h k2 E) = W_4S^(h k2)
-  for (int q = tid; q < L4; q += NT) {
-    const int k1 = q / S, s = q % S;
-    twF[q] = __ldg(&twPy[s * (4 * k1 + h)]);
-    twI[q] = __ldg(&twPy[k1 * (4 * s + h)]);
-  }
-  if (tid < E) twA[tid] = __ldg(&twPy[h * tid * S]);
-  if (tid < S) twB[tid] = __ldg(&twPy[h * tid * E]);
-  __syncthreads();
 
-  // the tensor entries of this CTA's columns (qy = 4k + h and Py - 4k - h,
-  // classes h and -h mod 4) into L2, so the z stage's loads do not wait on HBM
+  // folds: CTA h loads a quarter of the plane's lines (both halves of each
+  // column) and stores x[y] + (-i)^j x[y + L4] into line slot y of CTA j
+  const int LQ = (nlines + 3) >> 2;
+  const int lb = min(nlines, h * LQ), le = min(nlines, lb + LQ);
+  // twiddle-table entries of this thread, loaded with the first fold loads
+  constexpr int NTW = (L4 + NT - 1) / NT;
+  float2 tf[NTW], ti[NTW];
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    const int q = tid + j * NT;
+    const int k1 = q / S, s = q % S;
+    tf[j] = q < L4 ? __ldg(&twPy[s * (4 * k1 + h)]) : make_float2(0.f, 0.f);
+    ti[j] = q < L4 ? __ldg(&twPy[k1 * (4 * s + h)]) : make_float2(0.f, 0.f);
+  }
+  const float2 ta = tid < E ? __ldg(&twPy[h * tid * S]) : make_float2(0.f, 0.f);
+  const float2 tb = tid < S ? __ldg(&twPy[h * tid * E]) : make_float2(0.f, 0.f);
+  {
+    const int cnt = (le - lb) * L4;
+    constexpr int kB = 12;  // column pairs per thread in flight (all of them for the bulk grid)
+    for (int base = 0; base < cnt; base += NT * kB) {
+      float2 a[kB], b[kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int e = base + tid + u * NT;
+        const int line = lb + e / L4, y = e % L4;
+        const float2* src = w1 + kxoff + (long)line * ny;
+        a[u] = (e < cnt && y < ny) ? __ldg(src + y) : make_float2(0.f, 0.f);
+        b[u] = (e < cnt && y + L4 < ny) ? __ldg(src + y + L4) : make_float2(0.f, 0.f);
+      }
+      if (base == 0) cluster_wait();  // every CTA of the cluster has started
+      float2* dst0 = const_cast<float2*>(cluster_map(plane, 0u));
+      float2* dst1 = const_cast<float2*>(cluster_map(plane, 1u));
+      float2* dst2 = const_cast<float2*>(cluster_map(plane, 2u));
+      float2* dst3 = const_cast<float2*>(cluster_map(plane, 3u));
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int e = base + tid + u * NT;
+        if (e >= cnt) break;
+        const int o = (lb + e / L4) * PITCH + e % L4;
+        dst0[o] = cadd(a[u], b[u]);
+        dst1[o] = make_float2(a[u].x + b[u].y, a[u].y - b[u].x);
+        dst2[o] = csub(a[u], b[u]);
+        dst3[o] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
+      }
+    }
+    if (cnt == 0) cluster_wait();
+  }
+  cluster_arrive_release();  // this CTA's folds are stored
+
+  // while the other CTAs finish theirs: the twiddle tables, and the tensor
+  // entries of this CTA's columns (qy = 4k + h and Py - 4k - h, classes h and
+  // -h mod 4) into L2, so the z stage's loads do not wait on HBM
+#pragma unroll
+  for (int j = 0; j < NTW; ++j) {
+    const int q = tid + j * NT;
+    if (q < L4) {
+      twF[q] = tf[j];
+      twI[q] = ti[j];
+    }
+  }
+  if (tid < E) twA[tid] = ta;
+  if (tid < S) twB[tid] = tb;
   {
     const int o4 = plane_oct4_rows(g);
     const long cls_bytes = (long)o4 * 6 * sizeof(float);
@@ -195,42 +247,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
       asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
     }
   }
-
-  // folds: CTA h loads a quarter of the plane's lines (both halves of each
-  // column) and stores x[y] + (-i)^j x[y + L4] into line slot y of CTA j
-  const int LQ = (nlines + 3) >> 2;
-  const int lb = min(nlines, h * LQ), le = min(nlines, lb + LQ);
-  cluster_wait();  // every CTA of the cluster has started
-  {
-    float2* dst0 = const_cast<float2*>(cluster_map(plane, 0u));
-    float2* dst1 = const_cast<float2*>(cluster_map(plane, 1u));
-    float2* dst2 = const_cast<float2*>(cluster_map(plane, 2u));
-    float2* dst3 = const_cast<float2*>(cluster_map(plane, 3u));
-    const int cnt = (le - lb) * L4;
-    constexpr int kB = 4;  // column pairs per thread in flight
-    for (int e0 = tid; e0 < cnt; e0 += NT * kB) {
-      float2 a[kB], b[kB];
-#pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        const int e = e0 + u * NT;
-        const int line = lb + e / L4, y = e % L4;
-        const float2* src = w1 + kxoff + (long)line * ny;
-        a[u] = (e < cnt && y < ny) ? __ldg(src + y) : make_float2(0.f, 0.f);
-        b[u] = (e < cnt && y + L4 < ny) ? __ldg(src + y + L4) : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        const int e = e0 + u * NT;
-        if (e >= cnt) break;
-        const int o = (lb + e / L4) * PITCH + e % L4;
-        dst0[o] = cadd(a[u], b[u]);
-        dst1[o] = make_float2(a[u].x + b[u].y, a[u].y - b[u].x);
-        dst2[o] = csub(a[u], b[u]);
-        dst3[o] = make_float2(a[u].x - b[u].y, a[u].y + b[u].x);
-      }
-    }
-  }
-  cluster_sync_all();
+  __syncthreads();          // tables
+  cluster_wait_acquire();   // every CTA's folds
 
   constexpr int LPR = NT / S;  // lines per round, S threads per line
   const int s = tid % S;
@@ -317,18 +335,21 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
   // radix-4 combination over the cluster for lines [lb, le)
   cluster_sync_all();
   {
-    const float2* u0 = cluster_map(plane, 0u);
-    const float2* u1 = cluster_map(plane, 1u);
-    const float2* u2 = cluster_map(plane, 2u);
-    const float2* u3 = cluster_map(plane, 3u);
+    // the other CTAs' partials through distributed shared memory, this CTA's own directly
+    const float2* u0 = h == 0 ? plane : cluster_map(plane, 0u);
+    const float2* u1 = h == 1 ? plane : cluster_map(plane, 1u);
+    const float2* u2 = h == 2 ? plane : cluster_map(plane, 2u);
+    const float2* u3 = h == 3 ? plane : cluster_map(plane, 3u);
     const int cnt = (le - lb) * L4;
     float2* dst = w2 + kxoff;
-    constexpr int kB = 6;  // outputs per thread in flight
-    for (int e0 = tid; e0 < cnt; e0 += NT * kB) {
+    constexpr int kB = L4 >= 256 ? 6 : 4;  // outputs per thread in flight
+    // uniform trip count: the arrive below is executed once by every thread,
+    // after its last read of another CTA's shared memory
+    for (int base = 0; base < cnt; base += NT * kB) {
       float2 a[kB][4];
 #pragma unroll
       for (int b = 0; b < kB; ++b) {
-        const int e = e0 + b * NT;
+        const int e = base + tid + b * NT;
         if (e < cnt) {
           const int o = (lb + e / L4) * PITCH + e % L4;
           a[b][0] = u0[o];
@@ -337,9 +358,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
           a[b][3] = u3[o];
         }
       }
+      if (base + NT * kB >= cnt) cluster_arrive_release();
 #pragma unroll
       for (int b = 0; b < kB; ++b) {
-        const int e = e0 + b * NT;
+        const int e = base + tid + b * NT;
         if (e >= cnt) break;
         const int line = lb + e / L4, y = e % L4;
         const float2 s02 = cadd(a[b][0], a[b][2]), d02 = csub(a[b][0], a[b][2]);
@@ -349,9 +371,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
         if (y + L4 < ny) row[y + L4] = make_float2(d02.x - d13.y, d02.y + d13.x);
       }
     }
+    if (cnt == 0) cluster_arrive_release();
   }
   // no CTA leaves while another may still read its shared memory
-  cluster_sync_all();
+  cluster_wait();
 }
 
 // ---------------------------------------------------------------------------

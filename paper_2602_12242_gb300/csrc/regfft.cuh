@@ -59,6 +59,56 @@ template <int N, bool INV> struct RegFft {
     }
   }
 };
+// 16 points as 4 x 4: four 4-point DFTs over n1 of x[4 n1 + n2], the twiddles
+// W_16^(n2 k1), four 4-point DFTs over n2; output k1 + 4 k2.  W_16^4 = -i and
+// W_16^(2, 6) = (+-1 - i)/sqrt 2 take no general complex multiply.
+template <bool INV> struct RegFft<16, INV> {
+  __device__ __forceinline__ static void run(float2* v) {
+    float2 a[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) a[n2][n1] = v[4 * n1 + n2];
+      Dft<4, INV, float2>::run(a[n2]);
+    }
+    const float c = (float)kSqrtHalf;
+    auto w1 = [](float2 x) {  // W_16^1
+      float2 w = c_w32[2];
+      if (INV) w.y = -w.y;
+      return cmul(x, w);
+    };
+    auto w3 = [](float2 x) {  // W_16^3
+      float2 w = c_w32[6];
+      if (INV) w.y = -w.y;
+      return cmul(x, w);
+    };
+    auto w2 = [c](float2 x) {  // W_16^2 = W_8^1
+      return INV ? make_float2(c * (x.x - x.y), c * (x.x + x.y)) : make_float2(c * (x.x + x.y), c * (x.y - x.x));
+    };
+    auto w6 = [c](float2 x) {  // W_16^6 = W_8^3
+      return INV ? make_float2(-c * (x.x + x.y), c * (x.x - x.y)) : make_float2(c * (x.y - x.x), -c * (x.x + x.y));
+    };
+    a[1][1] = w1(a[1][1]);
+    a[1][2] = w2(a[1][2]);
+    a[1][3] = w3(a[1][3]);
+    a[2][1] = w2(a[2][1]);
+    a[2][2] = cmul_mi<INV>(a[2][2]);
+    a[2][3] = w6(a[2][3]);
+    a[3][1] = w3(a[3][1]);
+    a[3][2] = w6(a[3][2]);
+    {
+      const float2 t = w1(a[3][3]);  // W_16^9 = -W_16^1
+      a[3][3] = make_float2(-t.x, -t.y);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      float2 b[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+      Dft<4, INV, float2>::run(b);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+    }
+  }
+};
 template <bool INV> struct RegFft<8, INV> {
   __device__ __forceinline__ static void run(float2* v) { Dft<8, INV, float2>::run(v); }
 };
