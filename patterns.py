@@ -1,6 +1,6 @@
 """Reports of the method's patterns against the plain FP32 path on one GPU.
 
-  python -m paper_2602_12242_gb300.patterns [--pairs N] [--epochs E] [--insteps S] [--out FILE]
+  python patterns.py [--pairs N] [--epochs E] [--insteps S] [--out FILE]
 
 learned: the conv-net surrogate trained on (m, H_demag) pairs from the FFT
   path on the learned workload (64x64x4 cells, smooth textures); held-out
@@ -11,17 +11,17 @@ adjoint: time of the recorded forward plus the reverse sweep against the
   plain forward run for the adjoint workload (128x128x1, 2000 RK4 steps,
   a checkpoint every 100).
 
-  python -m paper_2602_12242_gb300.patterns --trajectory film --steps 20000 --every 1000 --npz FILE
+  python patterns.py --trajectory film --steps 20000 --every 1000 --npz FILE
 
 trajectory: snapshots of m every --every RK4 steps of a workload from its
   seeded initial state (for the FP32-vs-FP64 divergence curve).
 
-  python -m paper_2602_12242_gb300.patterns --fft-mode-timing
+  python patterns.py --fft-mode-timing
 
 fft-mode timing: per-kernel time of the bulk RK4 step with FP32 x transforms
   and with the split-BF16 DFT-as-GEMM first x stage.
 
-  python -m paper_2602_12242_gb300.patterns --fno [--train-sims N] [--frames F] [--epochs E] [--batch B] [--out FILE]
+  python patterns.py --fno [--train-sims N] [--frames F] [--epochs E] [--batch B] [--out FILE]
 
 fno: the Fourier-neural-operator surrogate and the conv net trained on the
   same SP4 film pairs (160x40x1 cells of 3.125 nm; S-state, then random
@@ -29,12 +29,12 @@ fno: the Fourier-neural-operator surrogate and the conv net trained on the
   error, <m>(t) over 1 ns under the two SP4 fields with each network as the
   demag backend against the FFT run, and times.
 
-  python -m paper_2602_12242_gb300.patterns --fno-timing
+  python patterns.py --fno-timing
 
 fno timing: per-call time of FNO inference (1 field, 128 fields) and of one
   training step of 128 fields on the SP4 film grid.
 
-  python -m paper_2602_12242_gb300.patterns --mri
+  python patterns.py --mri
 
 mri: time to solution of RK4 and of the explicit-explicit MRI step on the SP4
   film with the stiffened 0.78125 nm grid (640x160x4), MRI at 5x the RK4 step,
@@ -47,10 +47,15 @@ import time
 import numpy as np
 import torch
 
-from . import _lib as L
-from . import inputs
-from .solver import Context, to_dev4
-from .surrogate import (FourierSurrogate, Surrogate, init_fno_params, init_params, make_dataset, normalizer_stats,
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+
+from paper_2602_12242_gb300 import _lib as L  # noqa: E402
+from paper_2602_12242_gb300 import inputs  # noqa: E402
+from paper_2602_12242_gb300.solver import Context, to_dev4  # noqa: E402
+from paper_2602_12242_gb300.surrogate import (FourierSurrogate, Surrogate, init_fno_params, init_params, make_dataset, normalizer_stats,
                         run_in_loop, time_batched, time_demag, train)
 
 
