@@ -269,14 +269,13 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
   }
   __syncthreads();
 
-  // z stage: warp w takes 32 columns of parity w / HW; the two warps of a
-  // column block (w and w + HW) meet at their own named barrier
+  // z stage: warp w takes 32 columns of one parity per round; the two warps
+  // of a column block (w and w + HW) meet at their own named barrier
   {
     constexpr int CB = L4 / 32;       // column blocks
     constexpr int HW = NT / 64;       // warps per parity
     static_assert(HW + 1 <= 16, "named barrier ids");
     const int warp = tid >> 5, lane = tid & 31;
-    const int p = warp / HW;
     const int bar = 1 + warp % HW;
     const int o4 = plane_oct4_rows(g);
     const long qzs = 4L * o4 * 6;
@@ -284,6 +283,9 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
     for (int cb0 = 0; cb0 < CB; cb0 += HW) {
       const int cb = cb0 + warp % HW;
       if (cb >= CB) break;  // both warps of the pair leave together
+      // the odd half costs more (twiddles, the final add): a warp takes the
+      // even and the odd half in alternate rounds
+      const int p = (warp / HW) ^ ((cb0 / HW) & 1);
       const int col = 32 * cb + lane;
       const int ky = 4 * col + h;
       const bool fy = ky > (Py >> 1);
