@@ -152,6 +152,7 @@ struct mx_ctx {
   float2* tw_yh = nullptr;        // W_{Py/2}^k, k < Py/2
   bool plane = false;             // per-kx plane kernel (kx-major spectra and tensor)
   bool quad = false;              // plane path uses the four-CTA y/z kernel (else the two-CTA one)
+  int xfk_grid = 1;               // persistent grid of the plane path's x forward kernel
   bool inject_wait_timeout = false;  // mx_inject_wait_timeout: the two-CTA kernel's bulk-copy wait runs out
   void* dft_a = nullptr;          // split-BF16 DFT matrices (MX_FFT_SPLIT_BF16)
   int yz_tile = 1;                // kx columns per block in the fused kernel

@@ -57,85 +57,109 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xfk_kernel(con
   constexpr int NT = 3 * kRows * S;
   extern __shared__ float2 sm[];
   const int ychunks = (g.ny + kRows - 1) / kRows;
-  const int z = blockIdx.x / ychunks;
-  const int y0 = (blockIdx.x % ychunks) * kRows;
+  const int nblk = g.nz * ychunks;
   const int tid = threadIdx.x;
-  // Ms m of rows y0 .. y0 + kRows - 1 as packed pairs z[n] = M[2n] + i M[2n+1];
-  // nx <= M, so only n < M/2 can be non-zero.  Every load of the thread is
-  // issued before the first is used.
+  // Persistent blocks: block b of rows (z, y0 .. y0 + kRows - 1) for
+  // b = blockIdx.x, blockIdx.x + gridDim.x, ...; the next block's rows are
+  // prefetched into L2 while this block's spectrum is written out.
+  // Ms m as packed pairs z[n] = M[2n] + i M[2n+1]; nx <= M, so only n < M/2
+  // can be non-zero.
   constexpr int HALF = M / 2;
   constexpr int NLD = (kRows * HALF + NT - 1) / NT;
-  float4 va[NLD], vb[NLD];
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    float4 va[NLD], vb[NLD];
+    {
+      const int z = b / ychunks, y0 = (b % ychunks) * kRows;
 #pragma unroll
-  for (int j = 0; j < NLD; ++j) {
-    const int e = tid + j * NT;
-    const int r = e / HALF, n = e % HALF;
-    const int y = y0 + r;
-    const bool in = e < kRows * HALF && y < g.ny;
-    const long cell = ((long)z * g.ny + (in ? y : 0)) * g.nx + 2 * n;
-    va[j] = (in && 2 * n < g.nx) ? __ldg(&m[cell]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    vb[j] = (in && 2 * n + 1 < g.nx) ? __ldg(&m[cell + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  float sa[NLD], sb[NLD];
+      for (int j = 0; j < NLD; ++j) {
+        const int e = tid + j * NT;
+        const int r = e / HALF, n = e % HALF;
+        const int y = y0 + r;
+        const bool in = e < kRows * HALF && y < g.ny;
+        const long cell = ((long)z * g.ny + (in ? y : 0)) * g.nx + 2 * n;
+        va[j] = (in && 2 * n < g.nx) ? __ldg(&m[cell]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vb[j] = (in && 2 * n + 1 < g.nx) ? __ldg(&m[cell + 1]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    const int z = b / ychunks, y0 = (b % ychunks) * kRows;
+    float sa[NLD], sb[NLD];
 #pragma unroll
-  for (int j = 0; j < NLD; ++j) sa[j] = sb[j] = ms;
-  if (ms_map) {
+    for (int j = 0; j < NLD; ++j) sa[j] = sb[j] = ms;
+    if (ms_map) {
+#pragma unroll
+      for (int j = 0; j < NLD; ++j) {
+        const int e = tid + j * NT;
+        const int r = e / HALF, n = e % HALF;
+        const int y = y0 + r;
+        const bool in = e < kRows * HALF && y < g.ny;
+        const long cell = ((long)z * g.ny + (in ? y : 0)) * g.nx + 2 * n;
+        if (in && 2 * n < g.nx) sa[j] = __ldg(&ms_map[cell]);
+        if (in && 2 * n + 1 < g.nx) sb[j] = __ldg(&ms_map[cell + 1]);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NLD; ++j) {
       const int e = tid + j * NT;
+      if (e >= kRows * HALF) break;
       const int r = e / HALF, n = e % HALF;
-      const int y = y0 + r;
-      const bool in = e < kRows * HALF && y < g.ny;
-      const long cell = ((long)z * g.ny + (in ? y : 0)) * g.nx + 2 * n;
-      if (in && 2 * n < g.nx) sa[j] = __ldg(&ms_map[cell]);
-      if (in && 2 * n + 1 < g.nx) sb[j] = __ldg(&ms_map[cell + 1]);
+      sm[(3 * r + 0) * P + n] = make_float2(sa[j] * va[j].x, sb[j] * vb[j].x);
+      sm[(3 * r + 1) * P + n] = make_float2(sa[j] * va[j].y, sb[j] * vb[j].y);
+      sm[(3 * r + 2) * P + n] = make_float2(sa[j] * va[j].z, sb[j] * vb[j].z);
     }
-  }
-#pragma unroll
-  for (int j = 0; j < NLD; ++j) {
-    const int e = tid + j * NT;
-    if (e >= kRows * HALF) break;
-    const int r = e / HALF, n = e % HALF;
-    sm[(3 * r + 0) * P + n] = make_float2(sa[j] * va[j].x, sb[j] * vb[j].x);
-    sm[(3 * r + 1) * P + n] = make_float2(sa[j] * va[j].y, sb[j] * vb[j].y);
-    sm[(3 * r + 2) * P + n] = make_float2(sa[j] * va[j].z, sb[j] * vb[j].z);
-  }
-  for (int e = tid; e < 3 * kRows * HALF; e += NT) sm[(e / HALF) * P + HALF + e % HALF] = make_float2(0.f, 0.f);
-  __syncthreads();
-  line_fft<E, S, false, false, true>(sm + (tid / S) * P, tid % S, twM);
-  __syncthreads();
-  // r2c output from the packed transform Z: pairs (k, M - k), 0 < k < M/2,
-  // with E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i and
-  // T = W_2M^k O give X[k] = E + T and X[M-k] = conj(E - T); k = 0 gives
-  // X[0] = Re Z[0] + Im Z[0] and X[M] = Re Z[0] - Im Z[0]; X[M/2] = conj Z[M/2].
-  // Each thread keeps one line (row r fastest, so eight lanes store 64
-  // contiguous bytes of the kx-major spectrum).
-  constexpr int NL = 3 * kRows;
-  static_assert(NT % NL == 0, "xfk thread count");
-  const int li = tid % NL;
-  const int r = li % kRows, c = li / kRows;
-  const int y = y0 + r;
-  if (y < g.ny) {
-    const long plane = 3L * g.nz * g.ny;  // one kx
-    const float2* L = sm + (3 * r + c) * P;
-    float2* dst = w1 + ((long)c * g.nz + z) * g.ny + y;
-#pragma unroll 4
-    for (int k = tid / NL; k <= M / 2; k += NT / NL) {
-      const float2 a = L[k];
-      if (k == 0) {
-        dst[0] = make_float2(a.x + a.y, 0.f);
-        dst[(long)M * plane] = make_float2(a.x - a.y, 0.f);
-      } else if (k == M / 2) {
-        dst[(long)k * plane] = cconj(a);
-      } else {
-        const float2 b = L[M - k];
-        const float2 Ev = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
-        const float2 O = make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x));
-        const float2 T = cmul(__ldg(&twP[k]), O);
-        dst[(long)k * plane] = cadd(Ev, T);
-        dst[(long)(M - k) * plane] = cconj(csub(Ev, T));
+    for (int e = tid; e < 3 * kRows * HALF; e += NT) sm[(e / HALF) * P + HALF + e % HALF] = make_float2(0.f, 0.f);
+    __syncthreads();
+    line_fft<E, S, false, false, true>(sm + (tid / S) * P, tid % S, twM);
+    __syncthreads();
+    {
+      // the next block's rows (kRows rows of nx float4, contiguous per row) into L2
+      const int bn = b + gridDim.x;
+      if (bn < nblk) {
+        const int zn = bn / ychunks, yn = (bn % ychunks) * kRows;
+        const int lines_per_row = (g.nx * 16 + 127) / 128;
+        for (int q = tid; q < kRows * lines_per_row; q += NT) {
+          const int r = q / lines_per_row, k = q % lines_per_row;
+          if (yn + r < g.ny) {
+            const char* a = reinterpret_cast<const char*>(m + ((long)zn * g.ny + yn + r) * g.nx) +
+                            min(k * 128, g.nx * 16 - 16);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+          }
+        }
       }
     }
+    // r2c output from the packed transform Z: pairs (k, M - k), 0 < k < M/2,
+    // with E = (Z[k] + conj Z[M-k]) / 2, O = (Z[k] - conj Z[M-k]) / 2i and
+    // T = W_2M^k O give X[k] = E + T and X[M-k] = conj(E - T); k = 0 gives
+    // X[0] = Re Z[0] + Im Z[0] and X[M] = Re Z[0] - Im Z[0]; X[M/2] = conj Z[M/2].
+    // Each thread keeps one line (row r fastest, so eight lanes store 64
+    // contiguous bytes of the kx-major spectrum).
+    constexpr int NL = 3 * kRows;
+    static_assert(NT % NL == 0, "xfk thread count");
+    const int li = tid % NL;
+    const int r = li % kRows, c = li / kRows;
+    const int y = y0 + r;
+    if (y < g.ny) {
+      const long plane = 3L * g.nz * g.ny;  // one kx
+      const float2* L = sm + (3 * r + c) * P;
+      float2* dst = w1 + ((long)c * g.nz + z) * g.ny + y;
+#pragma unroll 4
+      for (int k = tid / NL; k <= M / 2; k += NT / NL) {
+        const float2 a = L[k];
+        if (k == 0) {
+          dst[0] = make_float2(a.x + a.y, 0.f);
+          dst[(long)M * plane] = make_float2(a.x - a.y, 0.f);
+        } else if (k == M / 2) {
+          dst[(long)k * plane] = cconj(a);
+        } else {
+          const float2 bv = L[M - k];
+          const float2 Ev = make_float2(0.5f * (a.x + bv.x), 0.5f * (a.y - bv.y));
+          const float2 O = make_float2(0.5f * (a.y + bv.y), -0.5f * (a.x - bv.x));
+          const float2 T = cmul(__ldg(&twP[k]), O);
+          dst[(long)k * plane] = cadd(Ev, T);
+          dst[(long)(M - k) * plane] = cconj(csub(Ev, T));
+        }
+      }
+    }
+    __syncthreads();  // the lines are read before the next block overwrites them
   }
 }
 
@@ -463,6 +487,10 @@ static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
   if (setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(xfk_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     MX_CUDA_TRY(cudaFuncSetAttribute(xik_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0, nsm = 0;
+    MX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xfk_kernel<E, S>, 3 * kRows * S, sm));
+    MX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    ctx->xfk_grid = (per_sm > 0 ? per_sm : 1) * nsm;
     constexpr int M = E * S;
     std::vector<float2> t(M);
     for (int k = 0; k < E; ++k)
@@ -477,7 +505,9 @@ static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
   const Grid& g = ctx->g;
   const int nblk = g.nz * ((g.ny + kRows - 1) / kRows);
   if (!inverse) {
-    xfk_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, ctx->tw_mk,
+    // persistent: as many blocks as fit on the device at once
+    const int grid = nblk < ctx->xfk_grid ? nblk : ctx->xfk_grid;
+    xfk_kernel<E, S><<<grid, 3 * kRows * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, ctx->tw_mk,
                                                        ctx->tw_x);
     return launch_check("xfk_kernel");
   }
