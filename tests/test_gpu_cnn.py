@@ -126,20 +126,41 @@ def test_training_reduces_loss_and_in_loop_fallback():
     assert res2["fallback_step"] is None and len(res2["errors"]) == 2
 
 
-def test_batched_surrogate_cost_per_field_against_fft():
-    """What the network gains over the method without it, in time: demag
-    fields for a batch of 64 textures of 64x64x4 cells, by the FFT convolution
-    field by field and by one batched surrogate forward.  The batched network
-    must cost less per field (its accuracy is the separate held-out check)."""
+def test_trained_surrogate_gain_against_fft():
+    """What the trained network gains over the method without it (Sec. II-D):
+    the conv net trained on FFT-path pairs of the learned workload (64x64x4
+    cells, smooth textures of bandwidth 8 cells) with a short schedule, then
+    its held-out relative L2 and its time per demag field against the FFT
+    convolution, one field at a time (as mx_heff's demag backend) and for a
+    batch of 64 fields.  The error gate is the level this schedule reaches
+    (0.147 on GB300, from 1.009 untrained); the longer training of the report
+    CLI reaches about 0.1.  The batched network must cost less per field than the FFT;
+    one field at a time it costs more, which the test reports."""
+    from paper_2602_12242_gb300 import _lib
     from paper_2602_12242_gb300 import inputs
-    from paper_2602_12242_gb300.solver import to_dev4
-    from paper_2602_12242_gb300.surrogate import Surrogate, time_batched
+    from paper_2602_12242_gb300.surrogate import (Surrogate, make_dataset, normalizer_stats, time_batched,
+                                                  time_demag, train)
     c = dict(inputs.CONFIGS["learned"])
     ctx = context(c)
-    M = torch.stack([to_dev4(inputs.smooth_texture((4, 64, 64), 8.0, 7000 + i)) for i in range(64)])
+    M, H = make_dataset(ctx, 2048, seed0=5000)
+    Mv, Hv = make_dataset(ctx, 128, seed0=95000)  # held out: textures the training never sees
     net = Surrogate(64, 64, 4, max_batch=64)
     net.set_params(torch.as_tensor(ocnn.init_params(5), dtype=torch.float32))
-    net.set_normalizer(STATS)
-    t = time_batched(ctx, net, M, reps=5)
-    print(f"\nper-field demag time, batch {t['batch']}: FFT {1e3 * t['fft']:.1f} us, surrogate {1e3 * t['surrogate']:.1f} us")
-    assert t["surrogate"] < t["fft"], t
+    net.set_normalizer(normalizer_stats(M, H))
+
+    def held_out():
+        return float(np.mean([_lib.mx_rel_l2(ctx.h, net.forward(Mv[i:i + 64]), Hv[i:i + 64])
+                              for i in range(0, Mv.shape[0], 64)]))
+
+    err0 = held_out()
+    losses = train(net, M, H, epochs=12, batch=64, lr=2e-3, milestones=(6, 9))
+    err = held_out()
+    one = time_demag(ctx, net, Mv[0].contiguous())
+    bat = time_batched(ctx, net, Mv[:64].contiguous(), reps=5)
+    print(f"\ntrained surrogate, learned workload 64x64x4: held-out relative L2 {err:.3f} "
+          f"(untrained {err0:.3f}; training loss {losses[0]:.3e} -> {losses[-1]:.3e}); "
+          f"one field: FFT {1e3 * one['fft']:.1f} us, surrogate {1e3 * one['surrogate']:.1f} us; "
+          f"per field in a batch of {bat['batch']}: FFT {1e3 * bat['fft']:.1f} us, "
+          f"surrogate {1e3 * bat['surrogate']:.1f} us")
+    assert err < 0.25 and err < 0.5 * err0, (err, err0)
+    assert bat["surrogate"] < bat["fft"], bat
