@@ -46,26 +46,38 @@ struct AdjWork {
   double* dms = nullptr;
   bool recorded = false;
   double dt = 0.0;
+  // Stored segments: the recompute of a segment keeps every step's three
+  // stage states and four demag fields, so the reverse step does not
+  // recompute them (used while they take at most kAdjStoreBytes).
+  float4* segst = nullptr;  // every x 3 stage states
+  float4* seghd = nullptr;  // every x 4 demag fields
+  float4* wbuf2 = nullptr;  // second (w, g_m) pair of the fused reverse kernels
+  float4* gm2 = nullptr;
+  // graphs of one full segment (forward, recompute, reverse), for graph_dt
+  cudaGraphExec_t g_fwd = nullptr, g_rec = nullptr, g_rev = nullptr;
+  double graph_dt = 0.0;
+  bool last_stored = false;  // the recorded forward left the last segment stored
 };
+
+constexpr double kAdjStoreBytes = 4.0e9;
 
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+// Per-cell pieces of the reverse stage, shared by the separate and the fused kernels.
+//
+// prep: for state m (stencil), its demag field hd and the cotangent v of
+// its stage rate, g_m = c [H x v + alpha (v (m.H) + H (v.m) - 2 m (v.H))] and
+// w = g_H / Ms with g_H = c [v x m + alpha (m (v.m) - v |m|^2)].
 template <bool DMI>
-__global__ void __launch_bounds__(256) adj_prep_kernel(const float4* __restrict__ m, const float4* __restrict__ hd,
-                                                       const float4* __restrict__ lam_k, Grid g, LocalCoef c,
-                                                       float4* __restrict__ wbuf, float4* __restrict__ gm) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return;
-  const long idx = ((long)k * g.ny + j) * g.nx + i;
+__device__ __forceinline__ void prep_cell(const float4* __restrict__ m, const float4* __restrict__ hd, const Grid& g,
+                                          const LocalCoef& c, int i, int j, int k, long idx, float3 v,
+                                          float4* __restrict__ wbuf, float4* __restrict__ gm) {
   const float3 mc = f3(m[idx]);
   const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
   Terms t;
   local_terms<DMI>(m, hd, g, c, i, j, k, idx, mc, 1.f / ms, t);
   const float3 H = t.demag + t.exch + t.anis + t.dmi + t.zee;
-  const float3 v = f3(lam_k[idx]);
   const float mH = dot3(mc, H), vm = dot3(v, mc), vH = dot3(v, H), mm = dot3(mc, mc);
   float3 gmv = c.alpha * (mH * v + vm * H - (2.f * vH) * mc);
   float3 gh = c.alpha * (vm * mc - mm * v);
@@ -79,19 +91,15 @@ __global__ void __launch_bounds__(256) adj_prep_kernel(const float4* __restrict_
   wbuf[idx] = make_float4(gh.x, gh.y, gh.z, 0.f);
 }
 
-// STAGE 3, 2, 1: renormalised stage input; STAGE 0: the step's start state.
+// finish: lam_m = g_m + Ms (L w) (w's stencil and hdw, the demag field of
+// w); the Ms gradient term; the stage's share of lam_acc; returns the next
+// stage rate's cotangent (STAGE 3, 2, 1) or zero (STAGE 0).
 template <bool DMI, int STAGE>
-__global__ void __launch_bounds__(256) adj_finish_kernel(const float4* __restrict__ m, const float4* __restrict__ wbuf,
-                                                         const float4* __restrict__ hdw,
-                                                         const float4* __restrict__ gm,
-                                                         const float4* __restrict__ lam_u4,
-                                                         float4* __restrict__ lam_acc, float4* __restrict__ lam_k,
-                                                         double* __restrict__ dms, Grid g, LocalCoef c, float dt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i >= g.nx || j >= g.ny) return;
-  const long idx = ((long)k * g.ny + j) * g.nx + i;
+__device__ __forceinline__ float3 finish_cell(const float4* __restrict__ m, const float4* __restrict__ wbuf,
+                                              const float4* __restrict__ hdw, const float4* __restrict__ gm,
+                                              const float4* __restrict__ lam_u4, float4* __restrict__ lam_acc,
+                                              double* __restrict__ dms, const Grid& g, const LocalCoef& c, float dt,
+                                              int i, int j, int k, long idx) {
   const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
   const float inv_ms = 1.f / ms;
   // L applied to w = g_H / Ms: demag from the convolution, local terms here
@@ -114,17 +122,86 @@ __global__ void __launch_bounds__(256) adj_finish_kernel(const float4* __restric
   if (STAGE == 0) {
     const float4 a = lam_acc[idx];
     lam_acc[idx] = make_float4(a.x + lam_m.x, a.y + lam_m.y, a.z + lam_m.z, 0.f);
-  } else {
-    // J_N(u_s)^T lam_m with n = m (unit), |u_s| in m.w
-    const float3 lu = (1.f / m4.w) * (lam_m - dot3(mc, lam_m) * mc);
-    const float4 a = lam_acc[idx];
-    lam_acc[idx] = make_float4(a.x + lu.x, a.y + lu.y, a.z + lu.z, 0.f);
-    const float3 u4 = f3(lam_u4[idx]);
-    const float cu4 = (STAGE == 1) ? dt / 6.f : dt / 3.f;
-    const float cus = (STAGE == 3) ? dt : 0.5f * dt;
-    const float3 nk = cu4 * u4 + cus * lu;
-    lam_k[idx] = make_float4(nk.x, nk.y, nk.z, 0.f);
+    return make_float3(0.f, 0.f, 0.f);
   }
+  // J_N(u_s)^T lam_m with n = m (unit), |u_s| in m.w
+  const float3 lu = (1.f / m4.w) * (lam_m - dot3(mc, lam_m) * mc);
+  const float4 a = lam_acc[idx];
+  lam_acc[idx] = make_float4(a.x + lu.x, a.y + lu.y, a.z + lu.z, 0.f);
+  const float3 u4 = f3(lam_u4[idx]);
+  const float cu4 = (STAGE == 1) ? dt / 6.f : dt / 3.f;
+  const float cus = (STAGE == 3) ? dt : 0.5f * dt;
+  return cu4 * u4 + cus * lu;
+}
+
+template <bool DMI>
+__global__ void __launch_bounds__(256) adj_prep_kernel(const float4* __restrict__ m, const float4* __restrict__ hd,
+                                                       const float4* __restrict__ lam_k, Grid g, LocalCoef c,
+                                                       float4* __restrict__ wbuf, float4* __restrict__ gm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  prep_cell<DMI>(m, hd, g, c, i, j, k, idx, f3(lam_k[idx]), wbuf, gm);
+}
+
+// STAGE 3, 2, 1: renormalised stage input; STAGE 0: the step's start state.
+template <bool DMI, int STAGE>
+__global__ void __launch_bounds__(256) adj_finish_kernel(const float4* __restrict__ m, const float4* __restrict__ wbuf,
+                                                         const float4* __restrict__ hdw,
+                                                         const float4* __restrict__ gm,
+                                                         const float4* __restrict__ lam_u4,
+                                                         float4* __restrict__ lam_acc, float4* __restrict__ lam_k,
+                                                         double* __restrict__ dms, Grid g, LocalCoef c, float dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  const float3 nk = finish_cell<DMI, STAGE>(m, wbuf, hdw, gm, lam_u4, lam_acc, dms, g, c, dt, i, j, k, idx);
+  if (STAGE > 0) lam_k[idx] = make_float4(nk.x, nk.y, nk.z, 0.f);
+}
+
+// Fused: begin of the reverse step (lam_u4 = J_N(u4)^T lam, lam_acc = lam_u4,
+// stage-4 cotangent dt/6 lam_u4) and prep of the last stage state m3.
+template <bool DMI>
+__global__ void __launch_bounds__(256) adj_begin_prep_kernel(const float4* __restrict__ mnew,
+                                                             const float4* __restrict__ m3,
+                                                             const float4* __restrict__ hd3,
+                                                             float4* __restrict__ lam_acc, float4* __restrict__ lam_u4,
+                                                             float4* __restrict__ wbuf, float4* __restrict__ gm,
+                                                             Grid g, LocalCoef c, float dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  const float4 n4 = mnew[idx];
+  const float3 nc = f3(n4);
+  const float3 l = f3(lam_acc[idx]);
+  const float3 lu = (1.f / n4.w) * (l - dot3(nc, l) * nc);
+  lam_u4[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+  lam_acc[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+  prep_cell<DMI>(m3, hd3, g, c, i, j, k, idx, (dt / 6.f) * lu, wbuf, gm);
+}
+
+// Fused: finish of stage STAGE (3, 2, 1) and prep of stage STAGE - 1, whose
+// cotangent is the value just computed at the same cell.  w and g_m of the
+// next stage go to the other buffer pair, because finish reads w's stencil.
+template <bool DMI, int STAGE>
+__global__ void __launch_bounds__(256) adj_finish_prep_kernel(
+    const float4* __restrict__ m, const float4* __restrict__ wbuf, const float4* __restrict__ hdw,
+    const float4* __restrict__ gm, const float4* __restrict__ lam_u4, float4* __restrict__ lam_acc,
+    double* __restrict__ dms, const float4* __restrict__ m_prev, const float4* __restrict__ hd_prev,
+    float4* __restrict__ wbuf_out, float4* __restrict__ gm_out, Grid g, LocalCoef c, float dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const long idx = ((long)k * g.ny + j) * g.nx + i;
+  const float3 nk = finish_cell<DMI, STAGE>(m, wbuf, hdw, gm, lam_u4, lam_acc, dms, g, c, dt, i, j, k, idx);
+  prep_cell<DMI>(m_prev, hd_prev, g, c, i, j, k, idx, nk, wbuf_out, gm_out);
 }
 
 // lam_u4 = J_N(u4)^T lam (m_new carries |u4| in w); lam_acc = lam_u4; lam_k = dt/6 lam_u4
@@ -166,11 +243,23 @@ static void adj_dims(const Grid& g, dim3& grid, dim3& block) {
 
 bool adjoint_recorded(const mx_ctx* ctx) { return ctx->adj && ctx->adj->recorded; }
 
+static void drop_graphs(AdjWork* w) {
+  for (cudaGraphExec_t* gp : {&w->g_fwd, &w->g_rec, &w->g_rev}) {
+    if (*gp) cudaGraphExecDestroy(*gp);
+    *gp = nullptr;
+  }
+}
+
+void adjoint_invalidate_graphs(mx_ctx* ctx) {
+  if (ctx->adj) drop_graphs(ctx->adj);
+}
+
 void adjoint_free(mx_ctx* ctx) {
   AdjWork* w = ctx->adj;
   if (!w) return;
+  drop_graphs(w);
   void* ptrs[] = {w->ckpt, w->seg, w->st, w->hd4, w->raw, w->lam_acc, w->lam_u4, w->lam_k, w->wbuf, w->gm, w->hdw,
-                  w->dms};
+                  w->dms, w->segst, w->seghd, w->wbuf2, w->gm2};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete w;
@@ -208,6 +297,12 @@ mx_status adjoint_reserve(mx_ctx* ctx, int nsteps, int every) {
   alloc((void**)&w->gm, sizeof(float4) * nc);
   alloc((void**)&w->hdw, sizeof(float4) * nc);
   alloc((void**)&w->dms, sizeof(double) * nc);
+  if (7.0 * w->every * nc * sizeof(float4) <= kAdjStoreBytes) {
+    alloc((void**)&w->segst, sizeof(float4) * nc * 3 * w->every);
+    alloc((void**)&w->seghd, sizeof(float4) * nc * 4 * w->every);
+    alloc((void**)&w->wbuf2, sizeof(float4) * nc);
+    alloc((void**)&w->gm2, sizeof(float4) * nc);
+  }
   if (!ok) {
     adjoint_free(ctx);
     set_error("mx_adjoint_reserve: device allocation failed");
@@ -216,23 +311,159 @@ mx_status adjoint_reserve(mx_ctx* ctx, int nsteps, int every) {
   return MX_OK;
 }
 
+// Capture what `enqueue` puts on a stream into an executable graph.
+template <typename F>
+static mx_status capture_graph(mx_ctx* ctx, cudaGraphExec_t* out, F enqueue) {
+  cudaGraph_t graph = nullptr;
+  MX_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const mx_status s = enqueue(ctx->cap_stream);
+  const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  if (s != MX_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("adjoint: capture failed: ") + cudaGetErrorString(e));
+    return MX_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    *out = nullptr;
+    set_error(std::string("adjoint: instantiate failed: ") + cudaGetErrorString(ei));
+    return MX_ERR_CUDA;
+  }
+  return MX_OK;
+}
+
+static bool graphs_usable(const mx_ctx* ctx) { return ctx->prof == nullptr; }
+
+// Stored segments.  Step i of the segment takes seg[i] to seg[i + 1]; its
+// stage states are segst[i][0..2] and the demag fields of seg[i] and the
+// three stage states seghd[i][0..3].
+static mx_status stored_recompute_step(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, cudaStream_t st) {
+  const long nc = ctx->g.ncell;
+  const float4* m = w->seg + (long)i * nc;
+  float4* S = w->segst + (long)i * 3 * nc;
+  float4* Hd = w->seghd + (long)i * 4 * nc;
+  const float4* states[4] = {m, S, S + nc, S + 2 * nc};
+  float4* outs[4] = {S, S + nc, S + 2 * nc, w->seg + (long)(i + 1) * nc};
+  const int modes[4] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3};
+  for (int q = 0; q < 4; ++q) {
+    if (demag) MX_TRY(demag_field(ctx, states[q], Hd + q * nc, st));
+    StageIO io{states[q], demag ? Hd + q * nc : nullptr, m, ctx->acc, outs[q], dt, MX_TERM_ALL};
+    MX_TRY(local_stage(ctx, modes[q], io, st));
+  }
+  return MX_OK;
+}
+
 mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, double dt, cudaStream_t st) {
   AdjWork* w = ctx->adj;
   const long nc = ctx->g.ncell;
   const size_t bytes = sizeof(float4) * nc;
+  if (w->graph_dt != dt) {
+    drop_graphs(w);
+    w->graph_dt = dt;
+  }
   MX_CUDA_TRY(cudaMemcpyAsync(w->raw, m0_raw, bytes, cudaMemcpyDeviceToDevice, st));
   float4* cur = w->seg;  // working state
   MX_CUDA_TRY(cudaMemcpyAsync(cur, m0_raw, bytes, cudaMemcpyDeviceToDevice, st));
   MX_TRY(normalize_field(ctx, cur, st));
-  for (int s = 0; s < w->nsteps; ++s) {
-    if (s % w->every == 0)
-      MX_CUDA_TRY(cudaMemcpyAsync(w->ckpt + (long)(s / w->every) * nc, cur, bytes, cudaMemcpyDeviceToDevice, st));
-    MX_TRY(rk4_step_direct(ctx, cur, dt, st));
+  const bool use_graph = graphs_usable(ctx);
+  const bool demag = ctx->p.demag != 0;
+  if (use_graph && !w->g_fwd && w->nsteps >= w->every) {
+    MX_TRY(capture_graph(ctx, &w->g_fwd, [&](cudaStream_t cs) -> mx_status {
+      for (int s = 0; s < w->every; ++s) MX_TRY(rk4_step_direct(ctx, cur, dt, cs));
+      return MX_OK;
+    }));
   }
-  MX_CUDA_TRY(cudaMemcpyAsync(m_final, cur, bytes, cudaMemcpyDeviceToDevice, st));
+  if (use_graph && w->segst && !w->g_rec && w->nsteps >= w->every) {
+    MX_TRY(capture_graph(ctx, &w->g_rec, [&](cudaStream_t cs) -> mx_status {
+      for (int i = 0; i < w->every; ++i) MX_TRY(stored_recompute_step(ctx, w, i, (float)dt, demag, cs));
+      return MX_OK;
+    }));
+  }
+  const float4* fin = cur;
+  for (int kseg = 0; kseg < w->nckpt; ++kseg) {
+    const int s0 = kseg * w->every;
+    const int len = (s0 + w->every < w->nsteps) ? w->every : w->nsteps - s0;
+    MX_CUDA_TRY(cudaMemcpyAsync(w->ckpt + (long)kseg * nc, cur, bytes, cudaMemcpyDeviceToDevice, st));
+    if (w->segst && kseg == w->nckpt - 1) {
+      // the last segment keeps its states and stage states: the reverse sweep
+      // starts on it without recomputing it
+      if (use_graph && len == w->every && w->g_rec) {
+        MX_CUDA_TRY(cudaGraphLaunch(w->g_rec, st));
+      } else {
+        for (int i = 0; i < len; ++i) MX_TRY(stored_recompute_step(ctx, w, i, (float)dt, demag, st));
+      }
+      fin = w->seg + (long)len * nc;
+    } else if (use_graph && len == w->every && w->g_fwd) {
+      MX_CUDA_TRY(cudaGraphLaunch(w->g_fwd, st));
+    } else {
+      for (int s = 0; s < len; ++s) MX_TRY(rk4_step_direct(ctx, cur, dt, st));
+    }
+  }
+  w->last_stored = w->segst != nullptr;
+  MX_CUDA_TRY(cudaMemcpyAsync(m_final, fin, bytes, cudaMemcpyDeviceToDevice, st));
   w->recorded = true;
   w->dt = dt;
   return MX_OK;
+}
+
+template <bool DMI>
+static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, cudaStream_t st) {
+  const Grid& g = ctx->g;
+  const long nc = g.ncell;
+  const LocalCoef c = local_coef(ctx);
+  dim3 grid, block;
+  adj_dims(g, grid, block);
+  const float4* m = w->seg + (long)i * nc;
+  const float4* mnew = m + nc;
+  const float4* S = w->segst + (long)i * 3 * nc;
+  const float4* Hd = w->seghd + (long)i * 4 * nc;
+  const float4* states[4] = {m, S, S + nc, S + 2 * nc};
+  float4* wb[2] = {w->wbuf, w->wbuf2};
+  float4* gmb[2] = {w->gm, w->gm2};
+  // demag fields of the stage states are zero without demag (hd4 cleared)
+  const float4* hd[4];
+  for (int q = 0; q < 4; ++q) hd[q] = demag ? Hd + q * nc : w->hd4;
+  adj_begin_prep_kernel<DMI><<<grid, block, 0, st>>>(mnew, states[3], hd[3], w->lam_acc, w->lam_u4, wb[0], gmb[0],
+                                                     g, c, dt);
+  MX_TRY(launch_check("adj_begin_prep_kernel"));
+  int b = 0;
+  for (int q = 3; q >= 0; --q) {
+    if (demag) MX_TRY(demag_field(ctx, wb[b], w->hdw, st));
+    switch (q) {
+      case 3:
+        adj_finish_prep_kernel<DMI, 3><<<grid, block, 0, st>>>(states[3], wb[b], w->hdw, gmb[b], w->lam_u4,
+                                                               w->lam_acc, w->dms, states[2], hd[2], wb[b ^ 1],
+                                                               gmb[b ^ 1], g, c, dt);
+        break;
+      case 2:
+        adj_finish_prep_kernel<DMI, 2><<<grid, block, 0, st>>>(states[2], wb[b], w->hdw, gmb[b], w->lam_u4,
+                                                               w->lam_acc, w->dms, states[1], hd[1], wb[b ^ 1],
+                                                               gmb[b ^ 1], g, c, dt);
+        break;
+      case 1:
+        adj_finish_prep_kernel<DMI, 1><<<grid, block, 0, st>>>(states[1], wb[b], w->hdw, gmb[b], w->lam_u4,
+                                                               w->lam_acc, w->dms, states[0], hd[0], wb[b ^ 1],
+                                                               gmb[b ^ 1], g, c, dt);
+        break;
+      default:
+        adj_finish_kernel<DMI, 0><<<grid, block, 0, st>>>(states[0], wb[b], w->hdw, gmb[b], w->lam_u4, w->lam_acc,
+                                                          w->lam_k, w->dms, g, c, dt);
+        break;
+    }
+    MX_TRY(launch_check("adj_finish_prep_kernel"));
+    b ^= 1;
+  }
+  return MX_OK;
+}
+
+static mx_status stored_reverse_step(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, bool dmi,
+                                     cudaStream_t st) {
+  return dmi ? stored_reverse_step_t<true>(ctx, w, i, dt, demag, st)
+             : stored_reverse_step_t<false>(ctx, w, i, dt, demag, st);
 }
 
 template <int STAGE>
@@ -264,6 +495,43 @@ mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0
   if (!demag) {
     MX_CUDA_TRY(cudaMemsetAsync(w->hd4, 0, 4 * bytes, st));
     MX_CUDA_TRY(cudaMemsetAsync(w->hdw, 0, bytes, st));
+  }
+  if (w->segst) {
+    // stored segments: recompute each segment keeping its stage states, then
+    // the fused reverse steps; full segments replay captured graphs
+    const bool use_graph = graphs_usable(ctx);
+    if (use_graph && w->nsteps >= w->every) {
+      if (!w->g_rec)
+        MX_TRY(capture_graph(ctx, &w->g_rec, [&](cudaStream_t cs) -> mx_status {
+          for (int i = 0; i < w->every; ++i) MX_TRY(stored_recompute_step(ctx, w, i, dt, demag, cs));
+          return MX_OK;
+        }));
+      if (!w->g_rev)
+        MX_TRY(capture_graph(ctx, &w->g_rev, [&](cudaStream_t cs) -> mx_status {
+          for (int i = w->every - 1; i >= 0; --i) MX_TRY(stored_reverse_step(ctx, w, i, dt, demag, dmi, cs));
+          return MX_OK;
+        }));
+    }
+    for (int kseg = w->nckpt - 1; kseg >= 0; --kseg) {
+      const int s0 = kseg * w->every;
+      const int len = (s0 + w->every < w->nsteps) ? w->every : w->nsteps - s0;
+      // the recorded forward left the last segment stored (first backward only)
+      const bool stored = w->last_stored && kseg == w->nckpt - 1;
+      if (!stored) {
+        MX_CUDA_TRY(cudaMemcpyAsync(w->seg, w->ckpt + (long)kseg * nc, bytes, cudaMemcpyDeviceToDevice, st));
+        if (use_graph && len == w->every && w->g_rec)
+          MX_CUDA_TRY(cudaGraphLaunch(w->g_rec, st));
+        else
+          for (int i = 0; i < len; ++i) MX_TRY(stored_recompute_step(ctx, w, i, dt, demag, st));
+      }
+      if (use_graph && len == w->every && w->g_rev)
+        MX_CUDA_TRY(cudaGraphLaunch(w->g_rev, st));
+      else
+        for (int i = len - 1; i >= 0; --i) MX_TRY(stored_reverse_step(ctx, w, i, dt, demag, dmi, st));
+    }
+    w->last_stored = false;  // the segment buffers now hold the first segment
+    adj_end_kernel<<<nb, 256, 0, st>>>(w->raw, w->lam_acc, grad_m0, w->dms, grad_ms, nc);
+    return launch_check("adj_end_kernel");
   }
   float4* st1 = w->st;
   float4* st2 = w->st + nc;

@@ -89,6 +89,7 @@ static mx_status check_ctx(const mx_ctx* ctx) {
 }
 
 static void invalidate_graph(mx_ctx* ctx) {
+  adjoint_invalidate_graphs(ctx);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   ctx->graph = nullptr;
   ctx->graph_m = nullptr;

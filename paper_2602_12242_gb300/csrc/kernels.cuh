@@ -72,6 +72,8 @@ mx_status build_demag_kernel(mx_ctx* ctx, cudaStream_t st);
 // adjoint.cu
 mx_status adjoint_reserve(mx_ctx* ctx, int nsteps, int every);
 void adjoint_free(mx_ctx* ctx);
+// drop the adjoint's captured graphs (material maps, bias or profiling changed)
+void adjoint_invalidate_graphs(mx_ctx* ctx);
 mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, double dt, cudaStream_t st);
 mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0, float* grad_ms, cudaStream_t st);
 bool adjoint_recorded(const mx_ctx* ctx);
