@@ -178,7 +178,7 @@ def algorithmic_bytes(cfg, P, ms_map=False, ku_map=False, axis_map=False):
 CSRC = os.path.join(ROOT, "paper_2602_12242_gb300", "csrc")
 # translation unit that defines each kernel of the traffic table
 KERNEL_TU = {"yzq_kernel": "demag_quad.cu", "yzh_kernel": "demag_plane.cu", "xfk_kernel": "demag_plane.cu",
-             "xik_kernel": "demag_plane.cu", "local_kernel": "local.cu"}
+             "xik_kernel": "demag_plane.cu", "xil_kernel": "demag_plane.cu", "local_kernel": "local.cu"}
 
 
 def kernel_sources(kernel):

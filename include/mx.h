@@ -74,7 +74,12 @@ typedef enum {
  *           on a cluster of four CTAs per plane where it fits, else the one
  *           on two CTAs; MX_ERR_UNSUPPORTED at mx_create if the grid fits
  *           neither); MX_DEMAG_PLANE_PAIR forces the per-kx-plane path with
- *           the two-CTA y/z kernel
+ *           the two-CTA y/z kernel; MX_DEMAG_PLANE_XLOCAL forces the
+ *           per-kx-plane path and, in the RK4 and Euler steps of
+ *           mx_rk_step, fuses the inverse x pass into the local stage
+ *           (H_demag stays in shared memory; mx_heff, mx_llg_rhs and
+ *           mx_energy still run the separate passes); needs fft_mode
+ *           MX_FFT_FP32
  *   fft_mode  MX_FFT_FP32 (default): every FFT stage in FP32 on the CUDA
  *           cores; MX_FFT_SPLIT_BF16: the first radix-32 stage of the x
  *           transforms runs as a DFT-as-GEMM on the tensor cores with operands
@@ -100,7 +105,8 @@ typedef struct {
 } mx_params;
 
 /* Demag convolution schedules for mx_params.demag_path. */
-enum { MX_DEMAG_AUTO = 0, MX_DEMAG_GENERIC = 1, MX_DEMAG_PLANE = 2, MX_DEMAG_PLANE_PAIR = 3 };
+enum { MX_DEMAG_AUTO = 0, MX_DEMAG_GENERIC = 1, MX_DEMAG_PLANE = 2, MX_DEMAG_PLANE_PAIR = 3,
+       MX_DEMAG_PLANE_XLOCAL = 4 };
 
 /* Arithmetic of the demag FFT stages for mx_params.fft_mode. */
 enum { MX_FFT_FP32 = 0, MX_FFT_SPLIT_BF16 = 1 };
@@ -278,7 +284,8 @@ mx_status mx_demag_spectrum(mx_ctx *ctx, float *out, mx_stream_t stream);
  * the launch count.  Arrays hold max_kernels.
  *   mx_kernel_slot(q)         the slot's role in the step ("x_fwd",
  *                             "yz_fused" for the y/z passes, "x_inv",
- *                             "local_stage", ...), the same for every context;
+ *                             "local_stage", "x_inv_local" for the fused
+ *                             inverse x pass and local stage, ...), the same for every context;
  *   mx_kernel_name(ctx, q)    the kernel that this context's schedule
  *                             launches in that slot (e.g. "yzq_kernel");
  *                             "" for an unknown slot or a NULL ctx. */

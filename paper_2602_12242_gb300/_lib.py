@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "MX_OK", 1: "MX_ERR_INVALID_ARG", 2: "MX_ERR_CUDA", 3: "MX_ER
 MX_TERM_DEMAG, MX_TERM_EXCH, MX_TERM_ANIS, MX_TERM_DMI, MX_TERM_ZEEMAN = 1, 2, 4, 8, 16
 MX_TERM_ALL = 31
 MX_RK4, MX_EULER, MX_MRI = 0, 1, 2
-MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE, MX_DEMAG_PLANE_PAIR = 0, 1, 2, 3
+MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE, MX_DEMAG_PLANE_PAIR, MX_DEMAG_PLANE_XLOCAL = 0, 1, 2, 3, 4
 MX_FFT_FP32, MX_FFT_SPLIT_BF16 = 0, 1
 
 

@@ -16,8 +16,9 @@ static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
 
-static const char* kNames[KID_COUNT] = {"x_fwd", "yz_fused", "y_fwd", "z_mul", "y_inv", "x_inv",
-                                        "local_stage", "normalize", "copy", "mri_slow", "mri_fast"};
+static const char* kNames[KID_COUNT] = {"x_fwd",     "yz_fused", "y_fwd",    "z_mul",    "y_inv",
+                                        "x_inv",     "local_stage", "normalize", "copy", "mri_slow",
+                                        "mri_fast", "x_inv_local"};
 const char* kernel_name(int id) { return (id >= 0 && id < KID_COUNT) ? kNames[id] : ""; }
 
 // ---------------------------------------------------------------------------
@@ -111,10 +112,15 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
   if (method == MX_MRI) return mri_step(ctx, m, dt, st);
   const bool demag = ctx->p.demag != 0;
   float4* hd = demag ? ctx->hd : nullptr;
+  const bool xlocal = demag && ctx->xlocal;
   if (method == MX_EULER) {
-    if (demag) MX_TRY(demag_field(ctx, m, hd, st));
     StageIO io{m, hd, m, ctx->acc, ctx->sa, (float)dt, MX_TERM_ALL};
-    MX_TRY(local_stage(ctx, LM_EULER, io, st));
+    if (xlocal) {
+      MX_TRY(plane_stage_xlocal(ctx, LM_EULER, io, st));
+    } else {
+      if (demag) MX_TRY(demag_field(ctx, m, hd, st));
+      MX_TRY(local_stage(ctx, LM_EULER, io, st));
+    }
     return copy_field(ctx, m, ctx->sa, st);
   }
   // RK4: m -> sa -> sb -> sa -> m
@@ -122,8 +128,12 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
   float4* out[4] = {ctx->sa, ctx->sb, ctx->sa, m};
   const int modes[4] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3};
   for (int s = 0; s < 4; ++s) {
-    if (demag) MX_TRY(demag_field(ctx, in[s], hd, st));
     StageIO io{in[s], hd, m, ctx->acc, out[s], (float)dt, MX_TERM_ALL};
+    if (xlocal) {
+      MX_TRY(plane_stage_xlocal(ctx, modes[s], io, st));
+      continue;
+    }
+    if (demag) MX_TRY(demag_field(ctx, in[s], hd, st));
     MX_TRY(local_stage(ctx, modes[s], io, st));
   }
   return MX_OK;
@@ -184,6 +194,7 @@ const char* mx_kernel_name(const mx_ctx* ctx, int q) {
     case KID_COPY: return "copy_kernel";
     case KID_MRI_SLOW: return "mri_slow_kernel";
     case KID_MRI_FAST: return "mri_fast_kernel";
+    case KID_X_INV_LOCAL: return ctx->xlocal ? "xil_kernel" : "";
     default: return "";
   }
 }
@@ -208,8 +219,9 @@ mx_status mx_create(mx_ctx** out, const mx_params* p) {
     set_error("mx_create: need dx, dy, dz, Ms, gamma > 0 and A, alpha >= 0");
     return MX_ERR_INVALID_ARG;
   }
-  if (p->demag_path < MX_DEMAG_AUTO || p->demag_path > MX_DEMAG_PLANE_PAIR) {
-    set_error("mx_create: demag_path must be MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE or MX_DEMAG_PLANE_PAIR");
+  if (p->demag_path < MX_DEMAG_AUTO || p->demag_path > MX_DEMAG_PLANE_XLOCAL) {
+    set_error("mx_create: demag_path must be MX_DEMAG_AUTO, MX_DEMAG_GENERIC, MX_DEMAG_PLANE, MX_DEMAG_PLANE_PAIR "
+              "or MX_DEMAG_PLANE_XLOCAL");
     return MX_ERR_INVALID_ARG;
   }
   if (p->fft_mode != MX_FFT_FP32 && p->fft_mode != MX_FFT_SPLIT_BF16) {

@@ -29,6 +29,7 @@
 #include "kernels.cuh"
 #include "bulk.cuh"
 #include "cluster.cuh"
+#include "local.cuh"
 #include "regfft.cuh"
 
 namespace mx {
@@ -166,17 +167,15 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xfk_kernel(con
 // ---------------------------------------------------------------------------
 // x inverse from the kx-major spectrum.
 // ---------------------------------------------------------------------------
+// The c2r transforms of rows (z, y0 .. y0 + kRows - 1), all three components,
+// into shared memory: afterwards element n of line 3 r + c holds H_c of cells
+// 2n (real part) and 2n + 1 (imaginary part) of row y0 + r.
 template <int E, int S>
-__global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(const float2* __restrict__ w2, Grid g,
-                                                            float4* __restrict__ hd, const float2* __restrict__ twM,
-                                                            const float2* __restrict__ twP) {
+__device__ __forceinline__ void xik_lines(float2* sm, const float2* __restrict__ w2, const Grid& g, int z, int y0,
+                                          const float2* __restrict__ twM, const float2* __restrict__ twP) {
   constexpr int M = E * S;
   constexpr int P = LineFft<E, S>::kPitch + 1;
   constexpr int NT = 3 * kRows * S;
-  extern __shared__ float2 sm[];
-  const int ychunks = (g.ny + kRows - 1) / kRows;
-  const int z = blockIdx.x / ychunks;
-  const int y0 = (blockIdx.x % ychunks) * kRows;
   const int tid = threadIdx.x;
   // c2r input from the half spectrum X: pairs (k, M - k) with S = X[k] +
   // conj X[M-k] and t = conj(W_2M^k) (X[k] - conj X[M-k]) give
@@ -223,8 +222,22 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(con
   __syncthreads();
   line_fft<E, S, true, false, true>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
+}
+
+template <int E, int S>
+__global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(const float2* __restrict__ w2, Grid g,
+                                                            float4* __restrict__ hd, const float2* __restrict__ twM,
+                                                            const float2* __restrict__ twP) {
+  constexpr int M = E * S;
+  constexpr int P = LineFft<E, S>::kPitch + 1;
+  constexpr int NT = 3 * kRows * S;
+  extern __shared__ float2 sm[];
+  const int ychunks = (g.ny + kRows - 1) / kRows;
+  const int z = blockIdx.x / ychunks;
+  const int y0 = (blockIdx.x % ychunks) * kRows;
+  xik_lines<E, S>(sm, w2, g, z, y0, twM, twP);
   // cells 2n and 2n + 1 of row r are the real and imaginary parts of element n
-  for (int e = tid; e < kRows * (M / 2); e += NT) {
+  for (int e = threadIdx.x; e < kRows * (M / 2); e += NT) {
     const int r = e / (M / 2), n = e % (M / 2);
     const int y = y0 + r, i = 2 * n;
     if (y >= g.ny || i >= g.nx) continue;
@@ -233,6 +246,46 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(con
     float4* row = hd + ((long)z * g.ny + y) * g.nx;
     row[i] = make_float4(hx.x, hy.x, hz.x, 0.f);
     if (i + 1 < g.nx) row[i + 1] = make_float4(hx.y, hy.y, hz.y, 0.f);
+  }
+}
+
+// The inverse x pass fused with the local stage: the c2r transforms of a
+// block's rows stay in shared memory, and each cell of those rows takes its
+// demag term from there for the local fields, the LLG right-hand side and
+// the stage update of `mode` (an RK4 stage or the Euler step), so H_demag
+// never goes to global memory.
+template <int MODE, bool DMI>
+__device__ __forceinline__ void xil_cells(const float2* sm, int P, int NT, const StageIO& io, const Grid& g,
+                                          const LocalCoef& c, int z, int y0, int* flag) {
+  const int rows = min(kRows, g.ny - y0);
+  for (int e = threadIdx.x; e < rows * g.nx; e += NT) {
+    const int r = e / g.nx, i = e - r * g.nx;
+    const float2* L = sm + 3 * r * P + (i >> 1);
+    const float2 hx = L[0], hy = L[P], hz = L[2 * P];
+    const float3 hdv = (i & 1) ? make_float3(hx.y, hy.y, hz.y) : make_float3(hx.x, hy.x, hz.x);
+    const int y = y0 + r;
+    local_cell_v<MODE, DMI>(io, g, c, i, y, z, ((long)z * g.ny + y) * g.nx + i, hdv, flag);
+  }
+}
+
+template <int E, int S, bool DMI>
+__global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xil_kernel(const float2* __restrict__ w2, Grid g,
+                                                            const float2* __restrict__ twM,
+                                                            const float2* __restrict__ twP, StageIO io, LocalCoef c,
+                                                            int mode, int* flag) {
+  constexpr int P = LineFft<E, S>::kPitch + 1;
+  constexpr int NT = 3 * kRows * S;
+  extern __shared__ float2 sm[];
+  const int ychunks = (g.ny + kRows - 1) / kRows;
+  const int z = blockIdx.x / ychunks;
+  const int y0 = (blockIdx.x % ychunks) * kRows;
+  xik_lines<E, S>(sm, w2, g, z, y0, twM, twP);
+  switch (mode) {
+    case LM_RK4_S0: xil_cells<LM_RK4_S0, DMI>(sm, P, NT, io, g, c, z, y0, flag); break;
+    case LM_RK4_S1: xil_cells<LM_RK4_S1, DMI>(sm, P, NT, io, g, c, z, y0, flag); break;
+    case LM_RK4_S2: xil_cells<LM_RK4_S2, DMI>(sm, P, NT, io, g, c, z, y0, flag); break;
+    case LM_RK4_S3: xil_cells<LM_RK4_S3, DMI>(sm, P, NT, io, g, c, z, y0, flag); break;
+    default: xil_cells<LM_EULER, DMI>(sm, P, NT, io, g, c, z, y0, flag); break;
   }
 }
 
@@ -487,6 +540,8 @@ static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
   if (setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(xfk_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     MX_CUDA_TRY(cudaFuncSetAttribute(xik_kernel<E, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(xil_kernel<E, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(xil_kernel<E, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0, nsm = 0;
     MX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xfk_kernel<E, S>, 3 * kRows * S, sm));
     MX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -513,6 +568,31 @@ static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
   }
   xik_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(ctx->w2, g, hd, ctx->tw_mk, ctx->tw_x);
   return launch_check("xik_kernel");
+}
+
+template <int E, int S>
+static mx_status xl_run(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st) {
+  const Grid& g = ctx->g;
+  const int nblk = g.nz * ((g.ny + kRows - 1) / kRows);
+  const LocalCoef c = local_coef(ctx);
+  if (c.dmi)
+    xil_kernel<E, S, true><<<nblk, 3 * kRows * S, xk_smem<E, S>(), st>>>(ctx->w2, g, ctx->tw_mk, ctx->tw_x, io, c,
+                                                                         mode, ctx->flag);
+  else
+    xil_kernel<E, S, false><<<nblk, 3 * kRows * S, xk_smem<E, S>(), st>>>(ctx->w2, g, ctx->tw_mk, ctx->tw_x, io, c,
+                                                                          mode, ctx->flag);
+  return launch_check("xil_kernel");
+}
+
+static mx_status xl_pass(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st) {
+  switch (ctx->g.Px / 2) {
+    case 1024: return xl_run<32, 32>(ctx, mode, io, st);
+    case 512: return xl_run<32, 16>(ctx, mode, io, st);
+    case 256: return xl_run<16, 16>(ctx, mode, io, st);
+    case 128: return xl_run<16, 8>(ctx, mode, io, st);
+    case 64: return xl_run<8, 8>(ctx, mode, io, st);
+    default: return MX_ERR_UNSUPPORTED;
+  }
 }
 
 template <int E, int S, int P>
@@ -574,9 +654,14 @@ mx_status plane_setup(mx_ctx* ctx) {
   ctx->quad = xk && path != MX_DEMAG_PLANE_PAIR && quad_pass(ctx, nullptr, true) == MX_OK;
   ctx->plane = ctx->quad || (xk && yzh_pass(ctx, nullptr, true) == MX_OK);
   ctx->g.oct4 = ctx->quad ? 1 : 0;
+  ctx->xlocal = ctx->plane && path == MX_DEMAG_PLANE_XLOCAL;
   clear_error();
-  if ((path == MX_DEMAG_PLANE || path == MX_DEMAG_PLANE_PAIR) && !ctx->plane) {
+  if ((path == MX_DEMAG_PLANE || path == MX_DEMAG_PLANE_PAIR || path == MX_DEMAG_PLANE_XLOCAL) && !ctx->plane) {
     set_error("mx_create: the per-kx plane demag kernel does not support this grid");
+    return MX_ERR_UNSUPPORTED;
+  }
+  if (ctx->xlocal && ctx->p.fft_mode != MX_FFT_FP32) {
+    set_error("mx_create: MX_DEMAG_PLANE_XLOCAL needs fft_mode MX_FFT_FP32");
     return MX_ERR_UNSUPPORTED;
   }
   if (ctx->p.fft_mode == MX_FFT_SPLIT_BF16) {
@@ -605,6 +690,23 @@ mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
     MX_TRY(dft ? dft_x_pass(ctx, nullptr, hd, true, st, false) : xk_pass(ctx, nullptr, hd, true, st, false));
   }
   return MX_OK;
+}
+
+mx_status plane_stage_xlocal(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st) {
+  if (mode < LM_RK4_S0 || mode > LM_EULER) {
+    set_error("plane_stage_xlocal: bad mode");
+    return MX_ERR_INVALID_ARG;
+  }
+  {
+    ProfScope ps(ctx, KID_X_FWD, st);
+    MX_TRY(xk_pass(ctx, io.m, nullptr, false, st, false));
+  }
+  {
+    ProfScope ps(ctx, KID_YZ, st);
+    MX_TRY(ctx->quad ? quad_pass(ctx, st, false) : yzh_pass(ctx, st, false));
+  }
+  ProfScope ps(ctx, KID_X_INV_LOCAL, st);
+  return xl_pass(ctx, mode, io, st);
 }
 
 // plane-path octant (plane_octant_index) -> [comp][qz][qy][kx]

@@ -18,6 +18,7 @@ enum KernelId {
   KID_COPY,
   KID_MRI_SLOW,
   KID_MRI_FAST,
+  KID_X_INV_LOCAL,
   KID_COUNT
 };
 const char* kernel_name(int id);
@@ -45,6 +46,12 @@ mx_status fast_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cu
 // demag_plane.cu
 mx_status plane_setup(mx_ctx* ctx);
 mx_status plane_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st);
+// One RK4 or Euler stage on the plane path with the inverse x pass fused into
+// the local stage (ctx->xlocal): the forward x pass of io.m, the y/z pass,
+// then H_demag, the local fields, the LLG right-hand side and the update of
+// `mode` in one kernel (io.hd is not used).
+struct StageIO;
+mx_status plane_stage_xlocal(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t st);
 mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 
 // demag_quad.cu: the four-CTA y/z plane kernel (setup: check the grid fits and

@@ -90,16 +90,16 @@ __device__ __forceinline__ float3 unit_norm(float3 v, float& r) {
   return inv * v;
 }
 
-// One cell of the fused local stage: H_eff (demag term from io.hd), the LLG
+// One cell of the fused local stage: H_eff (demag term hdv), the LLG
 // right-hand side and the stage update of MODE (LocalMode), written to io.out.
 template <int MODE, bool DMI>
-__device__ __forceinline__ void local_cell(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j, int k,
-                                           long idx, int* flag) {
+__device__ __forceinline__ void local_cell_v(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j,
+                                             int k, long idx, float3 hdv, int* flag) {
   const float3 mc = f3(io.m[idx]);
   const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
   const float inv_ms = 1.f / ms;
   Terms t;
-  local_terms<DMI>(io.m, io.hd, g, c, i, j, k, idx, mc, inv_ms, t);
+  local_terms_v<DMI>(io.m, hdv, g, c, i, j, k, idx, mc, inv_ms, t);
   float3 out;
   float wout = 0.f;  // |u| of a renormalised stage output (used by the adjoint)
   if (MODE == LM_HEFF) {
@@ -132,6 +132,13 @@ __device__ __forceinline__ void local_cell(const StageIO& io, const Grid& g, con
   }
   if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, kFlagNonfinite);
   io.out[idx] = make_float4(out.x, out.y, out.z, wout);
+}
+
+// The same with the demag term read from io.hd (zero if io.hd is null).
+template <int MODE, bool DMI>
+__device__ __forceinline__ void local_cell(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j, int k,
+                                           long idx, int* flag) {
+  local_cell_v<MODE, DMI>(io, g, c, i, j, k, idx, io.hd ? f3(__ldg(&io.hd[idx])) : make_float3(0.f, 0.f, 0.f), flag);
 }
 
 }  // namespace mx

@@ -335,3 +335,53 @@ def test_each_demag_schedule_matches_oracle(name, path):
     ref = mm.demag_field(problem(c), t64(m)).numpy()
     assert rel_l2(h, ref) <= TOL_FIELD
     assert rel_max(h, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["ragged37x21x5", "mid40x300x3", "quad70x100x6", "quad50x200x9", "wide600x24x2"])
+@pytest.mark.parametrize("method", ["rk4", "euler"])
+def test_fused_inverse_x_local_stage_matches_oracle(name, method):
+    """MX_DEMAG_PLANE_XLOCAL (the inverse x pass and the local stage in one
+    kernel, H_demag kept in shared memory): short trajectories against the
+    oracle and against the same steps with the separate passes, ragged rows
+    (ny mod 8 != 0), odd nx and DMI with chiral edges included."""
+    from paper_2602_12242_gb300 import _lib
+    c = CASES[name]
+    m0 = f32(random_m(c, 23))
+    ctx = context(c, demag_path=_lib.MX_DEMAG_PLANE_XLOCAL)
+    assert ctx.kernel_name("x_inv_local") == "xil_kernel"
+    dt, n = 1e-14, 4
+    m = gpu_m(m0)
+    ctx.rk_step(m, n, dt, method)
+    ctx.sync()
+    got = host(m)
+    ref = mm.run(problem(c), t64(m0), dt, n, method).numpy()
+    assert np.abs(got - ref).max() <= 1e-4
+    assert np.abs(np.linalg.norm(got, axis=-1) - 1).max() <= 1e-6
+    sep = context(c, demag_path=_lib.MX_DEMAG_PLANE)
+    assert sep.kernel_name("x_inv_local") == ""
+    m2 = gpu_m(m0)
+    sep.rk_step(m2, n, dt, method)
+    sep.sync()
+    assert np.abs(got - host(m2)).max() <= 1e-6
+
+
+def test_fused_inverse_x_local_stage_bulk_workload():
+    """The bulk workload at full size (512x512x16, grains): RK4 steps with the
+    fused inverse x + local kernel equal the separate passes to FP32 rounding,
+    the fused kernel is the one that runs, and |m| = 1 afterwards."""
+    from paper_2602_12242_gb300 import _lib, inputs
+    c = dict(inputs.CONFIGS["bulk"])
+    m0 = f32(inputs.initial_m("bulk"))
+    Ms, Ku, axis = inputs.material("bulk")
+    out = []
+    for path in (_lib.MX_DEMAG_PLANE_XLOCAL, _lib.MX_DEMAG_PLANE):
+        ctx = context(c, Ms=Ms, Ku=Ku, axis=f32(axis), demag_path=path)
+        m = gpu_m(m0)
+        prof = ctx.profile_step(m, 2, c["dt"])
+        if path == _lib.MX_DEMAG_PLANE_XLOCAL:
+            assert prof["x_inv_local"][1] == 8 and "x_inv" not in prof and "local_stage" not in prof
+        ctx.sync()
+        out.append(host(m))
+        del ctx
+    assert np.abs(out[0] - out[1]).max() <= 1e-6
+    assert np.abs(np.linalg.norm(out[0], axis=-1) - 1).max() <= 1e-6
