@@ -38,11 +38,12 @@ __device__ __forceinline__ void neighbours(const float4* __restrict__ m, const G
   zm = (k > 0) ? f3(__ldg(&m[idx - sz])) : mc;
 }
 
-// All field terms at cell (i, j, k); the demag term is the given value hdv.
+// All field terms at cell (i, j, k); the demag term is the given value hdv,
+// the easy axis e and the anisotropy coefficient cK = 2 Ku / mu0 are given.
 template <bool DMI>
-__device__ __forceinline__ void local_terms_v(const float4* __restrict__ m, float3 hdv, const Grid& g,
-                                              const LocalCoef& c, int i, int j, int k, long idx, float3 mc,
-                                              float inv_ms, Terms& t) {
+__device__ __forceinline__ void local_terms_ek(const float4* __restrict__ m, float3 hdv, const Grid& g,
+                                               const LocalCoef& c, int i, int j, int k, long idx, float3 mc,
+                                               float inv_ms, float3 e, float cK, Terms& t) {
   float3 xm, xp, ym, yp, zm, zp;
   neighbours(m, g, c, i, j, k, idx, mc, xp, xm, yp, ym, zp, zm);
   const float3 two = 2.f * mc;
@@ -55,11 +56,24 @@ __device__ __forceinline__ void local_terms_v(const float4* __restrict__ m, floa
   } else {
     t.dmi = make_float3(0.f, 0.f, 0.f);
   }
-  const float3 e = c.axis_map ? f3(__ldg(&c.axis_map[idx])) : make_float3(c.ax, c.ay, c.az);
-  const float cK = c.ku_map ? (__ldg(&c.ku_map[idx]) * (float)(2.0 / kMu0)) : c.cK;
   t.anis = (cK * inv_ms * dot3(mc, e)) * e;
   t.zee = make_float3(c.hx, c.hy, c.hz);
   t.demag = hdv;
+}
+
+__device__ __forceinline__ float3 easy_axis(const LocalCoef& c, long idx) {
+  return c.axis_map ? f3(__ldg(&c.axis_map[idx])) : make_float3(c.ax, c.ay, c.az);
+}
+__device__ __forceinline__ float aniso_coef(const LocalCoef& c, long idx) {
+  return c.ku_map ? (__ldg(&c.ku_map[idx]) * (float)(2.0 / kMu0)) : c.cK;
+}
+
+// All field terms at cell (i, j, k); the demag term is the given value hdv.
+template <bool DMI>
+__device__ __forceinline__ void local_terms_v(const float4* __restrict__ m, float3 hdv, const Grid& g,
+                                              const LocalCoef& c, int i, int j, int k, long idx, float3 mc,
+                                              float inv_ms, Terms& t) {
+  local_terms_ek<DMI>(m, hdv, g, c, i, j, k, idx, mc, inv_ms, easy_axis(c, idx), aniso_coef(c, idx), t);
 }
 
 // All field terms at cell (i, j, k), the demag term read from hd (zero if hd is null).
@@ -90,16 +104,39 @@ __device__ __forceinline__ float3 unit_norm(float3 v, float& r) {
   return inv * v;
 }
 
-// One cell of the fused local stage: H_eff (demag term hdv), the LLG
-// right-hand side and the stage update of MODE (LocalMode), written to io.out.
+// What the local stage of MODE reads at the cell itself (the neighbours
+// are read while the fields are formed).
+struct CellIn {
+  float3 m, m0, acc, e;
+  float ms, cK;
+};
+
+template <int MODE>
+__device__ __forceinline__ CellIn load_cell(const StageIO& io, const LocalCoef& c, long idx) {
+  CellIn v;
+  v.m = f3(io.m[idx]);
+  v.ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
+  v.e = easy_axis(c, idx);
+  v.cK = aniso_coef(c, idx);
+  if (MODE == LM_RK4_S1 || MODE == LM_RK4_S2 || MODE == LM_RK4_S3) {
+    v.m0 = f3(io.m0[idx]);
+    v.acc = f3(io.acc[idx]);
+  } else {
+    v.m0 = v.acc = make_float3(0.f, 0.f, 0.f);
+  }
+  return v;
+}
+
+// One cell of the fused local stage from its loaded inputs v: H_eff (demag
+// term hdv), the LLG right-hand side and the stage update of MODE
+// (LocalMode), written to io.out.
 template <int MODE, bool DMI>
-__device__ __forceinline__ void local_cell_v(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j,
-                                             int k, long idx, float3 hdv, int* flag) {
-  const float3 mc = f3(io.m[idx]);
-  const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
-  const float inv_ms = 1.f / ms;
+__device__ __forceinline__ void local_cell_in(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j,
+                                              int k, long idx, float3 hdv, const CellIn& v, int* flag) {
+  const float3 mc = v.m;
+  const float inv_ms = 1.f / v.ms;
   Terms t;
-  local_terms_v<DMI>(io.m, hdv, g, c, i, j, k, idx, mc, inv_ms, t);
+  local_terms_ek<DMI>(io.m, hdv, g, c, i, j, k, idx, mc, inv_ms, v.e, v.cK, t);
   float3 out;
   float wout = 0.f;  // |u| of a renormalised stage output (used by the adjoint)
   if (MODE == LM_HEFF) {
@@ -120,8 +157,8 @@ __device__ __forceinline__ void local_cell_v(const StageIO& io, const Grid& g, c
       io.acc[idx] = make_float4(kk.x, kk.y, kk.z, 0.f);
       out = unit_norm(mc + (0.5f * io.dt) * kk, wout);
     } else {
-      const float3 m0 = f3(io.m0[idx]);
-      const float3 a = f3(io.acc[idx]);
+      const float3 m0 = v.m0;
+      const float3 a = v.acc;
       if (MODE == LM_RK4_S3) {
         out = unit_norm(m0 + (io.dt * (1.f / 6.f)) * (a + kk), wout);
       } else {
@@ -132,6 +169,13 @@ __device__ __forceinline__ void local_cell_v(const StageIO& io, const Grid& g, c
   }
   if (!(isfinite(out.x) && isfinite(out.y) && isfinite(out.z))) atomicOr(flag, kFlagNonfinite);
   io.out[idx] = make_float4(out.x, out.y, out.z, wout);
+}
+
+// The same with the inputs loaded here.
+template <int MODE, bool DMI>
+__device__ __forceinline__ void local_cell_v(const StageIO& io, const Grid& g, const LocalCoef& c, int i, int j,
+                                             int k, long idx, float3 hdv, int* flag) {
+  local_cell_in<MODE, DMI>(io, g, c, i, j, k, idx, hdv, load_cell<MODE>(io, c, idx), flag);
 }
 
 // The same with the demag term read from io.hd (zero if io.hd is null).
