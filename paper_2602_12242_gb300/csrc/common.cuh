@@ -44,6 +44,32 @@ inline mx_status launch_check(const char* what) {
   return MX_OK;
 }
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be
+// scheduled while the kernel before it in the stream is still running; it
+// calls pdl_wait() before its first access to memory that kernel writes or
+// reads (the wait returns once that kernel has completed and its writes are
+// visible; without a programmatic dependency it returns at once).
+// pdl_trigger() lets the next launch_pdl kernel be scheduled as soon as every
+// CTA of this one has executed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);  // errors reach launch_check
+}
+
 // ---------------------------------------------------------------------------
 // Complex arithmetic on float2 / double2.
 // ---------------------------------------------------------------------------

@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(3 * R * S) xf_kernel(const float4* __restrict_
   const int nrows = g.ny * g.nz;
   const int row0 = blockIdx.x * R;
   const int tid = threadIdx.x;
+  pdl_wait();
   // batches of kB cell pairs per thread: 2 kB independent loads in flight
   constexpr int kB = 4;
   for (int e0 = tid; e0 < R * M; e0 += NT * kB) {
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(3 * R * S) xi_kernel(const float2* __restrict_
   const int row0 = blockIdx.x * R;
   const int tid = threadIdx.x;
   const long cs = (long)g.nz * g.ny * g.Hx;
+  pdl_wait();
   // batches of kB elements per thread: 2 kB independent loads in flight
   constexpr int kB = 4;
   for (int e0 = tid; e0 < 3 * R * M; e0 += NT * kB) {
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(6 * T * S) yz2d_kernel(float2* __restrict__ w1
     twS[q] = __ldg(&twH[(q % S) * (q / S)]);
     twS2[q] = __ldg(&twPy[q]);
   }
+  pdl_wait();  // the tables are constants; w1 is the previous kernel's
   __syncthreads();
   // line (c, t, h) at ((c T + t) 2 + h) PITCH
   for (int e = tid; e < 3 * T * LH; e += NT) {
@@ -231,8 +234,8 @@ static mx_status yz2d_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(yz2d_kernel<E, S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
-  yz2d_kernel<E, S, T><<<(ctx->g.Hx + T - 1) / T, 6 * T * S, sm, st>>>(ctx->w1, ctx->g, ctx->nhat, ctx->tw_yh,
-                                                                      ctx->tw_y);
+  launch_pdl(yz2d_kernel<E, S, T>, dim3((ctx->g.Hx + T - 1) / T), dim3(6 * T * S), sm, st, ctx->w1, ctx->g,
+             ctx->nhat, ctx->tw_yh, ctx->tw_y);
   return launch_check("yz2d_kernel");
 }
 
@@ -263,8 +266,8 @@ static mx_status run_xf(mx_ctx* ctx, const float4* m, cudaStream_t st, bool setu
   }
   const Grid& g = ctx->g;
   const int nrows = g.ny * g.nz;
-  xf_kernel<E, S, R><<<(nrows + R - 1) / R, 3 * R * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1,
-                                                                 ctx->tw_m, ctx->tw_x);
+  launch_pdl(xf_kernel<E, S, R>, dim3((nrows + R - 1) / R), dim3(3 * R * S), sm, st, m, g, (float)ctx->p.Ms,
+             ctx->ms_map, ctx->w1, ctx->tw_m, ctx->tw_x);
   return launch_check("xf_kernel");
 }
 
@@ -277,7 +280,8 @@ static mx_status run_xi(mx_ctx* ctx, float4* hd, cudaStream_t st, bool setup) {
   }
   const Grid& g = ctx->g;
   const int nrows = g.ny * g.nz;
-  xi_kernel<E, S, R><<<(nrows + R - 1) / R, 3 * R * S, sm, st>>>(ctx->w1, g, hd, ctx->tw_m, ctx->tw_x);
+  launch_pdl(xi_kernel<E, S, R>, dim3((nrows + R - 1) / R), dim3(3 * R * S), sm, st, ctx->w1, g, hd, ctx->tw_m,
+             ctx->tw_x);
   return launch_check("xi_kernel");
 }
 

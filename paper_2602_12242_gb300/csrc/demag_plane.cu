@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xfk_kernel(con
   const int ychunks = (g.ny + kRows - 1) / kRows;
   const int nblk = g.nz * ychunks;
   const int tid = threadIdx.x;
+  pdl_wait();
   // Persistent blocks: block b of rows (z, y0 .. y0 + kRows - 1) for
   // b = blockIdx.x, blockIdx.x + gridDim.x, ...; the next block's rows are
   // prefetched into L2 while this block's spectrum is written out.
@@ -235,6 +236,7 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xik_kernel(con
   const int ychunks = (g.ny + kRows - 1) / kRows;
   const int z = blockIdx.x / ychunks;
   const int y0 = (blockIdx.x % ychunks) * kRows;
+  pdl_wait();
   xik_lines<E, S>(sm, w2, g, z, y0, twM, twP);
   // cells 2n and 2n + 1 of row r are the real and imaginary parts of element n
   for (int e = threadIdx.x; e < kRows * (M / 2); e += NT) {
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(3 * kRows * S, S >= 32 ? 1 : 2) xil_kernel(con
   const int ychunks = (g.ny + kRows - 1) / kRows;
   const int z = blockIdx.x / ychunks;
   const int y0 = (blockIdx.x % ychunks) * kRows;
+  pdl_wait();
   xik_lines<E, S>(sm, w2, g, z, y0, twM, twP);
   switch (mode) {
     case LM_RK4_S0: xil_cells<LM_RK4_S0, DMI>(sm, P, NT, io, g, c, z, y0, flag); break;
@@ -562,11 +565,11 @@ static mx_status xk_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
   if (!inverse) {
     // persistent: as many blocks as fit on the device at once
     const int grid = nblk < ctx->xfk_grid ? nblk : ctx->xfk_grid;
-    xfk_kernel<E, S><<<grid, 3 * kRows * S, sm, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, ctx->tw_mk,
-                                                       ctx->tw_x);
+    launch_pdl(xfk_kernel<E, S>, dim3(grid), dim3(3 * kRows * S), sm, st, m, g, (float)ctx->p.Ms, ctx->ms_map,
+               ctx->w1, ctx->tw_mk, ctx->tw_x);
     return launch_check("xfk_kernel");
   }
-  xik_kernel<E, S><<<nblk, 3 * kRows * S, sm, st>>>(ctx->w2, g, hd, ctx->tw_mk, ctx->tw_x);
+  launch_pdl(xik_kernel<E, S>, dim3(nblk), dim3(3 * kRows * S), sm, st, ctx->w2, g, hd, ctx->tw_mk, ctx->tw_x);
   return launch_check("xik_kernel");
 }
 
@@ -576,11 +579,11 @@ static mx_status xl_run(mx_ctx* ctx, int mode, const StageIO& io, cudaStream_t s
   const int nblk = g.nz * ((g.ny + kRows - 1) / kRows);
   const LocalCoef c = local_coef(ctx);
   if (c.dmi)
-    xil_kernel<E, S, true><<<nblk, 3 * kRows * S, xk_smem<E, S>(), st>>>(ctx->w2, g, ctx->tw_mk, ctx->tw_x, io, c,
-                                                                         mode, ctx->flag);
+    launch_pdl(xil_kernel<E, S, true>, dim3(nblk), dim3(3 * kRows * S), xk_smem<E, S>(), st, ctx->w2, g, ctx->tw_mk,
+               ctx->tw_x, io, c, mode, ctx->flag);
   else
-    xil_kernel<E, S, false><<<nblk, 3 * kRows * S, xk_smem<E, S>(), st>>>(ctx->w2, g, ctx->tw_mk, ctx->tw_x, io, c,
-                                                                          mode, ctx->flag);
+    launch_pdl(xil_kernel<E, S, false>, dim3(nblk), dim3(3 * kRows * S), xk_smem<E, S>(), st, ctx->w2, g,
+               ctx->tw_mk, ctx->tw_x, io, c, mode, ctx->flag);
   return launch_check("xil_kernel");
 }
 

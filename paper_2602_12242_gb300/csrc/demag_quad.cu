@@ -156,6 +156,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kQuadNT, 2)
   constexpr int NT = kQuadNT;
   constexpr int Q = P / 2;
   extern __shared__ __align__(16) float2 sm[];
+  pdl_wait();                // w1 is the previous kernel's
   cluster_arrive_relaxed();  // this CTA has started (waited for before the first remote store)
   const int h = (int)cluster_rank();
   const int kx = blockIdx.x >> 2;
@@ -394,7 +395,8 @@ static mx_status yzq_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(yzq_kernel<E, S, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
-  yzq_kernel<E, S, P><<<4 * ctx->g.Hx, kQuadNT, sm, st>>>(ctx->w1, ctx->w2, ctx->g, ctx->nhat, ctx->tw_y);
+  launch_pdl(yzq_kernel<E, S, P>, dim3(4 * ctx->g.Hx), dim3(kQuadNT), sm, st, ctx->w1, ctx->w2, ctx->g, ctx->nhat,
+             ctx->tw_y);
   return launch_check("yzq_kernel");
 }
 

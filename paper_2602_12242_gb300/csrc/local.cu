@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256) local_kernel(StageIO io, Grid g, LocalCoe
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
+  pdl_wait();
   if (i >= g.nx || j >= g.ny) return;
   const long idx = ((long)k * g.ny + j) * g.nx + i;
   local_cell<MODE, DMI>(io, g, c, i, j, k, idx, flag);
@@ -126,9 +127,9 @@ template <int MODE>
 static void launch_local(bool dmi, dim3 grid, dim3 block, cudaStream_t st, const StageIO& io, const Grid& g,
                          const LocalCoef& c, int* flag) {
   if (dmi)
-    local_kernel<MODE, true><<<grid, block, 0, st>>>(io, g, c, flag);
+    launch_pdl(local_kernel<MODE, true>, grid, block, 0, st, io, g, c, flag);
   else
-    local_kernel<MODE, false><<<grid, block, 0, st>>>(io, g, c, flag);
+    launch_pdl(local_kernel<MODE, false>, grid, block, 0, st, io, g, c, flag);
 }
 
 static void local_dims(const Grid& g, dim3& grid, dim3& block) {
