@@ -12,16 +12,26 @@
 
 namespace mx {
 
+// Threads of the x kernels' FFT phase: the 3R lines of S threads, rounded up
+// to whole warps (the extra threads transform scratch lines).  The load and
+// store phases use all NT >= that many threads, so that a block with few
+// rows still has many memory requests in flight.
+template <int S, int R> struct XfShape {
+  static constexpr int NF = (3 * R * S + 31) / 32 * 32;
+  static constexpr int lines = NF / S;  // shared-memory lines, scratch included
+};
+
 // ---------------------------------------------------------------------------
 // x forward (r2c), R rows per block, 3R lines of M = E*S points.
 // ---------------------------------------------------------------------------
-template <int E, int S, int R>
-__global__ void __launch_bounds__(3 * R * S) xf_kernel(const float4* __restrict__ m, Grid g, float ms,
-                                                       const float* __restrict__ ms_map, float2* __restrict__ w1,
-                                                       const float2* __restrict__ twM, const float2* __restrict__ twP) {
+template <int E, int S, int R, int NT>
+__global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Grid g, float ms,
+                                                const float* __restrict__ ms_map, float2* __restrict__ w1,
+                                                const float2* __restrict__ twM, const float2* __restrict__ twP) {
   constexpr int M = E * S;
   constexpr int P = LineFft<E, S>::kPitch;
-  constexpr int NT = 3 * R * S;
+  constexpr int NF = XfShape<S, R>::NF;
+  static_assert(NT >= NF && NT % 32 == 0, "xf thread count");
   extern __shared__ float2 sm[];
   const int nrows = g.ny * g.nz;
   const int row0 = blockIdx.x * R;
@@ -64,7 +74,7 @@ __global__ void __launch_bounds__(3 * R * S) xf_kernel(const float4* __restrict_
     }
   }
   __syncthreads();
-  line_fft<E, S, false>(sm + (tid / S) * P, tid % S, twM);
+  if (tid < NF) line_fft<E, S, false>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
   const long cs = (long)g.nz * g.ny * g.Hx;
   // batches of kB outputs per thread: the twiddle loads of a batch go out together
@@ -98,12 +108,13 @@ __global__ void __launch_bounds__(3 * R * S) xf_kernel(const float4* __restrict_
 // ---------------------------------------------------------------------------
 // x inverse (c2r).
 // ---------------------------------------------------------------------------
-template <int E, int S, int R>
-__global__ void __launch_bounds__(3 * R * S) xi_kernel(const float2* __restrict__ w1, Grid g, float4* __restrict__ hd,
-                                                       const float2* __restrict__ twM, const float2* __restrict__ twP) {
+template <int E, int S, int R, int NT>
+__global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, Grid g, float4* __restrict__ hd,
+                                                const float2* __restrict__ twM, const float2* __restrict__ twP) {
   constexpr int M = E * S;
   constexpr int P = LineFft<E, S>::kPitch;
-  constexpr int NT = 3 * R * S;
+  constexpr int NF = XfShape<S, R>::NF;
+  static_assert(NT >= NF && NT % 32 == 0, "xi thread count");
   extern __shared__ float2 sm[];
   const int nrows = g.ny * g.nz;
   const int row0 = blockIdx.x * R;
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(3 * R * S) xi_kernel(const float2* __restrict_
     }
   }
   __syncthreads();
-  line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
+  if (tid < NF) line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
   __syncthreads();
   for (int e = tid; e < R * g.nx; e += NT) {
     const int r = e / g.nx, i = e % g.nx;
@@ -163,14 +174,14 @@ __global__ void __launch_bounds__(3 * R * S) xi_kernel(const float2* __restrict_
 // restricted to y < ny is even + W_Py^-y odd.  Lines (c, t, half) of LH =
 // Py/2 points run the register line FFT, S threads each.
 // ---------------------------------------------------------------------------
-template <int E, int S, int T>
-__global__ void __launch_bounds__(6 * T * S) yz2d_kernel(float2* __restrict__ w1, Grid g,
-                                                         const float* __restrict__ nhat,
-                                                         const float2* __restrict__ twH,
-                                                         const float2* __restrict__ twPy) {
+template <int E, int S, int T, int NT>
+__global__ void __launch_bounds__(NT) yz2d_kernel(float2* __restrict__ w1, Grid g, const float* __restrict__ nhat,
+                                                  const float2* __restrict__ twH,
+                                                  const float2* __restrict__ twPy) {
   constexpr int LH = E * S;
   constexpr int PITCH = LineFft<E, S>::kPitch;
-  constexpr int NT = 6 * T * S;
+  constexpr int NF = 6 * T * S;  // threads of the FFT phases (whole warps, or S == 1)
+  static_assert(NT >= NF && NT % 32 == 0 && (NF % 32 == 0 || S == 1), "yz2d thread count");
   extern __shared__ __align__(16) float2 sm[];
   float2* twS = sm + 6 * T * PITCH;  // W_LH^(s k) at [k S + s]
   float2* twS2 = twS + LH;           // W_Py^y, y < LH
@@ -184,18 +195,29 @@ __global__ void __launch_bounds__(6 * T * S) yz2d_kernel(float2* __restrict__ w1
   }
   pdl_wait();  // the tables are constants; w1 is the previous kernel's
   __syncthreads();
-  // line (c, t, h) at ((c T + t) 2 + h) PITCH
-  for (int e = tid; e < 3 * T * LH; e += NT) {
-    const int t = e % T, y = (e / T) % LH, c = e / (T * LH);
-    const int kx = kx0 + t;
-    float2 v = make_float2(0.f, 0.f);
-    if (y < ny && kx < g.Hx) v = w1[c * wc + (long)y * g.Hx + kx];
-    float2* L = sm + ((c * T + t) * 2) * PITCH;
-    L[y] = v;
-    L[PITCH + y] = cmul(v, twS2[y]);
+  // line (c, t, h) at ((c T + t) 2 + h) PITCH; every load of a thread in flight at once
+  {
+    constexpr int NE = 3 * T * LH, KB = (NE + NT - 1) / NT;
+    float2 v[KB];
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int e = tid + u * NT;
+      const int t = e % T, y = (e / T) % LH, c = e / (T * LH);
+      const int kx = kx0 + t;
+      v[u] = (e < NE && y < ny && kx < g.Hx) ? w1[c * wc + (long)y * g.Hx + kx] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < KB; ++u) {
+      const int e = tid + u * NT;
+      if (e >= NE) break;
+      const int t = e % T, y = (e / T) % LH, c = e / (T * LH);
+      float2* L = sm + ((c * T + t) * 2) * PITCH;
+      L[y] = v[u];
+      L[PITCH + y] = cmul(v[u], twS2[y]);
+    }
   }
   __syncthreads();
-  line_fft<E, S, false, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
+  if (tid < NF) line_fft<E, S, false, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
   __syncthreads();
   const long no = (long)g.Hx * g.Oy * g.Oz;
   for (int e = tid; e < T * 2 * LH; e += NT) {
@@ -216,7 +238,7 @@ __global__ void __launch_bounds__(6 * T * S) yz2d_kernel(float2* __restrict__ w1
     *pz = make_float2(nzz * mz.x, nzz * mz.y);
   }
   __syncthreads();
-  line_fft<E, S, true, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
+  if (tid < NF) line_fft<E, S, true, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
   __syncthreads();
   for (int e = tid; e < 3 * T * ny; e += NT) {
     const int t = e % T, y = (e / T) % ny, c = e / (T * ny);
@@ -227,14 +249,16 @@ __global__ void __launch_bounds__(6 * T * S) yz2d_kernel(float2* __restrict__ w1
   }
 }
 
+// 384 threads per block at least: most of them only load, multiply and store
 template <int E, int S, int T>
 static mx_status yz2d_run(mx_ctx* ctx, cudaStream_t st, bool setup) {
+  constexpr int NT = 6 * T * S > 384 ? 6 * T * S : 384;
   const size_t sm = sizeof(float2) * (6 * T * LineFft<E, S>::kPitch + 2 * E * S);
   if (setup) {
-    MX_CUDA_TRY(cudaFuncSetAttribute(yz2d_kernel<E, S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(yz2d_kernel<E, S, T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
-  launch_pdl(yz2d_kernel<E, S, T>, dim3((ctx->g.Hx + T - 1) / T), dim3(6 * T * S), sm, st, ctx->w1, ctx->g,
+  launch_pdl(yz2d_kernel<E, S, T, NT>, dim3((ctx->g.Hx + T - 1) / T), dim3(NT), sm, st, ctx->w1, ctx->g,
              ctx->nhat, ctx->tw_yh, ctx->tw_y);
   return launch_check("yz2d_kernel");
 }
@@ -256,31 +280,33 @@ mx_status yz2d_pass(mx_ctx* ctx, cudaStream_t st) { return yz2d_dispatch(ctx, st
 // ---------------------------------------------------------------------------
 // Dispatch
 // ---------------------------------------------------------------------------
-template <int E, int S> static size_t x_smem(int R) { return sizeof(float2) * 3 * R * LineFft<E, S>::kPitch; }
-template <int E, int S, int R>
+template <int E, int S, int R> static size_t x_smem() {
+  return sizeof(float2) * XfShape<S, R>::lines * LineFft<E, S>::kPitch;
+}
+template <int E, int S, int R, int NT>
 static mx_status run_xf(mx_ctx* ctx, const float4* m, cudaStream_t st, bool setup) {
-  const size_t sm = x_smem<E, S>(R);
+  const size_t sm = x_smem<E, S, R>();
   if (setup) {
-    MX_CUDA_TRY(cudaFuncSetAttribute(xf_kernel<E, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(xf_kernel<E, S, R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
   const Grid& g = ctx->g;
   const int nrows = g.ny * g.nz;
-  launch_pdl(xf_kernel<E, S, R>, dim3((nrows + R - 1) / R), dim3(3 * R * S), sm, st, m, g, (float)ctx->p.Ms,
+  launch_pdl(xf_kernel<E, S, R, NT>, dim3((nrows + R - 1) / R), dim3(NT), sm, st, m, g, (float)ctx->p.Ms,
              ctx->ms_map, ctx->w1, ctx->tw_m, ctx->tw_x);
   return launch_check("xf_kernel");
 }
 
-template <int E, int S, int R>
+template <int E, int S, int R, int NT>
 static mx_status run_xi(mx_ctx* ctx, float4* hd, cudaStream_t st, bool setup) {
-  const size_t sm = x_smem<E, S>(R);
+  const size_t sm = x_smem<E, S, R>();
   if (setup) {
-    MX_CUDA_TRY(cudaFuncSetAttribute(xi_kernel<E, S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(xi_kernel<E, S, R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     return MX_OK;
   }
   const Grid& g = ctx->g;
   const int nrows = g.ny * g.nz;
-  launch_pdl(xi_kernel<E, S, R>, dim3((nrows + R - 1) / R), dim3(3 * R * S), sm, st, ctx->w1, g, hd, ctx->tw_m,
+  launch_pdl(xi_kernel<E, S, R, NT>, dim3((nrows + R - 1) / R), dim3(NT), sm, st, ctx->w1, g, hd, ctx->tw_m,
              ctx->tw_x);
   return launch_check("xi_kernel");
 }
@@ -288,22 +314,26 @@ static mx_status run_xi(mx_ctx* ctx, float4* hd, cudaStream_t st, bool setup) {
 // x pass for M = Px/2 (returns MX_ERR_UNSUPPORTED when no specialisation fits).
 // Each size has a many-rows-per-block variant and a few-rows one; grids whose
 // row count would give fewer than two blocks per SM with the first take the
-// second (set-up prepares both).
+// second (set-up prepares both).  The few-rows variant runs kFewRowsNT
+// threads, most of which only load and store.
 static constexpr int kMinBlocks = 2 * 152;
+static constexpr int kFewRowsNT = 192;
 
 template <int E, int S, int RB, int RS>
 static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
+  constexpr int NB = XfShape<S, RB>::NF;
+  constexpr int NS = XfShape<S, RS>::NF > kFewRowsNT ? XfShape<S, RS>::NF : kFewRowsNT;
   if (setup) {
-    mx_status s = run_xi<E, S, RB>(ctx, hd, st, true);
-    if (s == MX_OK) s = run_xf<E, S, RB>(ctx, m, st, true);
-    if (s == MX_OK) s = run_xi<E, S, RS>(ctx, hd, st, true);
-    if (s == MX_OK) s = run_xf<E, S, RS>(ctx, m, st, true);
+    mx_status s = run_xi<E, S, RB, NB>(ctx, hd, st, true);
+    if (s == MX_OK) s = run_xf<E, S, RB, NB>(ctx, m, st, true);
+    if (s == MX_OK) s = run_xi<E, S, RS, NS>(ctx, hd, st, true);
+    if (s == MX_OK) s = run_xf<E, S, RS, NS>(ctx, m, st, true);
     return s;
   }
   const int nrows = ctx->g.ny * ctx->g.nz;
   if ((nrows + RB - 1) / RB >= kMinBlocks)
-    return inverse ? run_xi<E, S, RB>(ctx, hd, st, false) : run_xf<E, S, RB>(ctx, m, st, false);
-  return inverse ? run_xi<E, S, RS>(ctx, hd, st, false) : run_xf<E, S, RS>(ctx, m, st, false);
+    return inverse ? run_xi<E, S, RB, NB>(ctx, hd, st, false) : run_xf<E, S, RB, NB>(ctx, m, st, false);
+  return inverse ? run_xi<E, S, RS, NS>(ctx, hd, st, false) : run_xf<E, S, RS, NS>(ctx, m, st, false);
 }
 
 static mx_status x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
