@@ -127,6 +127,21 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
   const float4* in[4] = {m, ctx->sa, ctx->sb, ctx->sa};
   float4* out[4] = {ctx->sa, ctx->sb, ctx->sa, m};
   const int modes[4] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3};
+  if (demag && ctx->xrow && !ctx->plane && !ctx->surrogate && !ctx->fno) {
+    // few-row grids: the forward x pass once, then per stage the y/z passes
+    // and one row kernel (inverse x, local stage, the next stage's forward x)
+    {
+      ProfScope ps(ctx, KID_X_FWD, st);
+      MX_TRY(fast_x_pass(ctx, m, nullptr, false, st));
+    }
+    for (int s = 0; s < 4; ++s) {
+      StageIO io{in[s], nullptr, m, ctx->acc, out[s], (float)dt, MX_TERM_ALL};
+      MX_TRY(demag_yz(ctx, st));
+      ProfScope ps(ctx, KID_X_INV_LOCAL, st);
+      MX_TRY(fast_row_stage(ctx, modes[s], io, s < 3, st));
+    }
+    return MX_OK;
+  }
   for (int s = 0; s < 4; ++s) {
     StageIO io{in[s], hd, m, ctx->acc, out[s], (float)dt, MX_TERM_ALL};
     if (xlocal) {
@@ -194,7 +209,7 @@ const char* mx_kernel_name(const mx_ctx* ctx, int q) {
     case KID_COPY: return "copy_kernel";
     case KID_MRI_SLOW: return "mri_slow_kernel";
     case KID_MRI_FAST: return "mri_fast_kernel";
-    case KID_X_INV_LOCAL: return ctx->xlocal ? "xil_kernel" : "";
+    case KID_X_INV_LOCAL: return ctx->xlocal ? "xil_kernel" : (ctx->xrow && !ctx->plane ? "xr_kernel" : "");
     default: return "";
   }
 }

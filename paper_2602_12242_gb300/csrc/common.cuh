@@ -180,6 +180,7 @@ struct mx_ctx {
   bool quad = false;              // plane path uses the four-CTA y/z kernel (else the two-CTA one)
   int xfk_grid = 1;               // persistent grid of the plane path's x forward kernel
   bool xlocal = false;            // inverse x pass fused into the RK/Euler local stage
+  bool xrow = false;              // few-row grids: inverse x, local stage and next forward x in one kernel
   bool inject_wait_timeout = false;  // mx_inject_wait_timeout: the two-CTA kernel's bulk-copy wait runs out
   void* dft_a = nullptr;          // split-BF16 DFT matrices (MX_FFT_SPLIT_BF16)
   int yz_tile = 1;                // kx columns per block in the fused kernel

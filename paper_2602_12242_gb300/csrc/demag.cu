@@ -316,25 +316,8 @@ mx_status demag_setup(mx_ctx* ctx) {
   return MX_OK;
 }
 
-mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st) {
-  if (ctx->surrogate) return cnn_demag(ctx->surrogate, m, hd, st);
-  if (ctx->fno) return fno_demag(ctx->fno, m, hd, st);
-  if (ctx->plane) return plane_field(ctx, m, hd, st);
+mx_status demag_yz(mx_ctx* ctx, cudaStream_t st) {
   const Grid& g = ctx->g;
-  const int rows = x_rows(g);
-  const int nrows = g.ny * g.nz;
-  const int M = g.Px > 1 ? g.Px / 2 : 1;
-  const size_t xs = sizeof(float2) * 3 * rows * M;
-  {
-    ProfScope ps(ctx, KID_X_FWD, st);
-    if (ctx->fast_x) {
-      MX_TRY(fast_x_pass(ctx, m, nullptr, false, st));
-    } else {
-      x_fwd_kernel<<<(nrows + rows - 1) / rows, kNT, xs, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1,
-                                                               ctx->tw_x, rows);
-      MX_TRY(launch_check("x_fwd_kernel"));
-    }
-  }
   if (ctx->yz2d) {
     ProfScope ps(ctx, KID_YZ, st);
     MX_TRY(yz2d_pass(ctx, st));
@@ -365,6 +348,29 @@ mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st)
       MX_TRY(launch_check("y_inv_kernel"));
     }
   }
+  return MX_OK;
+}
+
+mx_status demag_field(mx_ctx* ctx, const float4* m, float4* hd, cudaStream_t st) {
+  if (ctx->surrogate) return cnn_demag(ctx->surrogate, m, hd, st);
+  if (ctx->fno) return fno_demag(ctx->fno, m, hd, st);
+  if (ctx->plane) return plane_field(ctx, m, hd, st);
+  const Grid& g = ctx->g;
+  const int rows = x_rows(g);
+  const int nrows = g.ny * g.nz;
+  const int M = g.Px > 1 ? g.Px / 2 : 1;
+  const size_t xs = sizeof(float2) * 3 * rows * M;
+  {
+    ProfScope ps(ctx, KID_X_FWD, st);
+    if (ctx->fast_x) {
+      MX_TRY(fast_x_pass(ctx, m, nullptr, false, st));
+    } else {
+      x_fwd_kernel<<<(nrows + rows - 1) / rows, kNT, xs, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1,
+                                                               ctx->tw_x, rows);
+      MX_TRY(launch_check("x_fwd_kernel"));
+    }
+  }
+  MX_TRY(demag_yz(ctx, st));
   {
     ProfScope ps(ctx, KID_X_INV, st);
     if (ctx->fast_x) {

@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "local.cuh"
 #include "regfft.cuh"
 
 namespace mx {
@@ -21,22 +22,42 @@ template <int S, int R> struct XfShape {
   static constexpr int lines = NF / S;  // shared-memory lines, scratch included
 };
 
+// The 3R line transforms of M = E*S points of an x kernel's block, in place
+// in shared memory (line l at l * P), ending with a block barrier.  Where
+// every thread can take whole radix-8 butterflies (3RM / NT >= 8 elements
+// each) all NT threads run the Stockham passes of block_fft (short chains per
+// thread, a barrier per pass); otherwise the NF threads of the lines run the
+// two-step register transform (twM[q] = W_M^q either way).
+template <int E, int S, int R, int NT, bool INV>
+__device__ __forceinline__ void x_line_ffts(float2* sm, const float2* __restrict__ twM) {
+  constexpr int M = E * S;
+  constexpr int P = LineFft<E, S>::kPitch;
+  constexpr int EPT = 3 * R * M / NT;
+  if constexpr ((3 * R * M) % NT == 0 && EPT >= 8) {
+    block_fft<INV, float2, EPT, NT>(sm, M, 3 * R, lines1(P), 1, twM, 1);
+  } else {
+    if ((int)threadIdx.x < XfShape<S, R>::NF) line_fft<E, S, INV>(sm + (threadIdx.x / S) * P, threadIdx.x % S, twM);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // x forward (r2c), R rows per block, 3R lines of M = E*S points.
 // ---------------------------------------------------------------------------
-template <int E, int S, int R, int NT>
-__global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Grid g, float ms,
-                                                const float* __restrict__ ms_map, float2* __restrict__ w1,
-                                                const float2* __restrict__ twM, const float2* __restrict__ twP) {
+// Rows row0 .. row0 + R - 1 of Ms m (the real row packed as z[n] = x[2n] +
+// i x[2n+1]) through the line FFT and the split step into w1.  COHERENT reads
+// m with plain loads (m written earlier in the same kernel), else through the
+// read-only path.
+template <int E, int S, int R, int NT, bool COHERENT>
+__device__ __forceinline__ void xf_rows(float2* sm, const float4* __restrict__ m, const Grid& g, float ms,
+                                        const float* __restrict__ ms_map, float2* __restrict__ w1, int row0,
+                                        const float2* __restrict__ twM, const float2* __restrict__ twP) {
   constexpr int M = E * S;
   constexpr int P = LineFft<E, S>::kPitch;
   constexpr int NF = XfShape<S, R>::NF;
   static_assert(NT >= NF && NT % 32 == 0, "xf thread count");
-  extern __shared__ float2 sm[];
   const int nrows = g.ny * g.nz;
-  const int row0 = blockIdx.x * R;
   const int tid = threadIdx.x;
-  pdl_wait();
   // batches of kB cell pairs per thread: 2 kB independent loads in flight
   constexpr int kB = 4;
   for (int e0 = tid; e0 < R * M; e0 += NT * kB) {
@@ -53,11 +74,11 @@ __global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Gr
         const long cell = (long)row * g.nx;
         const int i0 = 2 * n, i1 = i0 + 1;
         if (i0 < g.nx) {
-          a[u] = __ldg(&m[cell + i0]);
+          a[u] = COHERENT ? m[cell + i0] : __ldg(&m[cell + i0]);
           if (ms_map) sa[u] = __ldg(&ms_map[cell + i0]);
         }
         if (i1 < g.nx) {
-          b[u] = __ldg(&m[cell + i1]);
+          b[u] = COHERENT ? m[cell + i1] : __ldg(&m[cell + i1]);
           if (ms_map) sb[u] = __ldg(&ms_map[cell + i1]);
         }
       }
@@ -74,8 +95,7 @@ __global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Gr
     }
   }
   __syncthreads();
-  if (tid < NF) line_fft<E, S, false>(sm + (tid / S) * P, tid % S, twM);
-  __syncthreads();
+  x_line_ffts<E, S, R, NT, false>(sm, twM);
   const long cs = (long)g.nz * g.ny * g.Hx;
   // batches of kB outputs per thread: the twiddle loads of a batch go out together
   constexpr int kBo = 4;
@@ -105,22 +125,31 @@ __global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Gr
   }
 }
 
+template <int E, int S, int R, int NT>
+__global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Grid g, float ms,
+                                                const float* __restrict__ ms_map, float2* __restrict__ w1,
+                                                const float2* __restrict__ twM, const float2* __restrict__ twP) {
+  extern __shared__ float2 sm[];
+  pdl_wait();
+  xf_rows<E, S, R, NT, false>(sm, m, g, ms, ms_map, w1, blockIdx.x * R, twM, twP);
+}
+
 // ---------------------------------------------------------------------------
 // x inverse (c2r).
 // ---------------------------------------------------------------------------
+// The c2r transforms of rows row0 .. row0 + R - 1 into shared memory:
+// afterwards element n of line 3 r + c holds H_c of cells 2n (real part) and
+// 2n + 1 (imaginary part) of row row0 + r.
 template <int E, int S, int R, int NT>
-__global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, Grid g, float4* __restrict__ hd,
-                                                const float2* __restrict__ twM, const float2* __restrict__ twP) {
+__device__ __forceinline__ void xi_rows(float2* sm, const float2* __restrict__ w1, const Grid& g, int row0,
+                                        const float2* __restrict__ twM, const float2* __restrict__ twP) {
   constexpr int M = E * S;
   constexpr int P = LineFft<E, S>::kPitch;
   constexpr int NF = XfShape<S, R>::NF;
   static_assert(NT >= NF && NT % 32 == 0, "xi thread count");
-  extern __shared__ float2 sm[];
   const int nrows = g.ny * g.nz;
-  const int row0 = blockIdx.x * R;
   const int tid = threadIdx.x;
   const long cs = (long)g.nz * g.ny * g.Hx;
-  pdl_wait();
   // batches of kB elements per thread: 2 kB independent loads in flight
   constexpr int kB = 4;
   for (int e0 = tid; e0 < 3 * R * M; e0 += NT * kB) {
@@ -149,20 +178,74 @@ __global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, G
     }
   }
   __syncthreads();
-  if (tid < NF) line_fft<E, S, true>(sm + (tid / S) * P, tid % S, twM);
-  __syncthreads();
-  for (int e = tid; e < R * g.nx; e += NT) {
+  x_line_ffts<E, S, R, NT, true>(sm, twM);
+}
+
+// H_demag of cell i of row r from the c2r lines
+template <int E, int S>
+__device__ __forceinline__ float3 xi_cell(const float2* sm, int r, int i) {
+  constexpr int P = LineFft<E, S>::kPitch;
+  const float2* L = sm + (3 * r) * P + (i >> 1);
+  const float2 hx = L[0], hy = L[P], hz = L[2 * P];
+  return (i & 1) ? make_float3(hx.y, hy.y, hz.y) : make_float3(hx.x, hy.x, hz.x);
+}
+
+template <int E, int S, int R, int NT>
+__global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, Grid g, float4* __restrict__ hd,
+                                                const float2* __restrict__ twM, const float2* __restrict__ twP) {
+  extern __shared__ float2 sm[];
+  const int nrows = g.ny * g.nz;
+  const int row0 = blockIdx.x * R;
+  pdl_wait();
+  xi_rows<E, S, R, NT>(sm, w1, g, row0, twM, twP);
+  for (int e = threadIdx.x; e < R * g.nx; e += NT) {
     const int r = e / g.nx, i = e % g.nx;
     const int row = row0 + r;
     if (row >= nrows) continue;
-    const float2* L = sm + (3 * r) * P;
-    const int n = i >> 1;
-    const bool odd = i & 1;
-    const float hx = odd ? L[n].y : L[n].x;
-    const float hy = odd ? L[P + n].y : L[P + n].x;
-    const float hz = odd ? L[2 * P + n].y : L[2 * P + n].x;
-    hd[(long)row * g.nx + i] = make_float4(hx, hy, hz, 0.f);
+    const float3 h = xi_cell<E, S>(sm, r, i);
+    hd[(long)row * g.nx + i] = make_float4(h.x, h.y, h.z, 0.f);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Row kernel of the RK4 step: the inverse x pass of rows row0 .. row0 + R - 1,
+// the local stage of `mode` on their cells (demag term from shared memory),
+// and, with `xf_next`, the forward x pass of the stage output io.out for the
+// next stage, so that between the y/z passes of two stages there is one
+// kernel and H_demag never goes to global memory.  io.out of the block's rows
+// is written by this block only and read back after a block barrier.
+// ---------------------------------------------------------------------------
+template <int MODE, bool DMI, int E, int S, int R, int NT>
+__device__ __forceinline__ void xr_cells(const float2* sm, const StageIO& io, const Grid& g, const LocalCoef& c,
+                                         int row0, int* flag) {
+  const int nrows = g.ny * g.nz;
+  for (int e = threadIdx.x; e < R * g.nx; e += NT) {
+    const int r = e / g.nx, i = e - r * g.nx;
+    const int row = row0 + r;
+    if (row >= nrows) continue;
+    const int z = row / g.ny, y = row - z * g.ny;
+    local_cell_v<MODE, DMI>(io, g, c, i, y, z, (long)row * g.nx + i, xi_cell<E, S>(sm, r, i), flag);
+  }
+}
+
+template <int E, int S, int R, int NT, bool DMI>
+__global__ void __launch_bounds__(NT) xr_kernel(float2* __restrict__ w1, Grid g, float ms,
+                                                const float* __restrict__ ms_map, const float2* __restrict__ twM,
+                                                const float2* __restrict__ twP, StageIO io, LocalCoef c, int mode,
+                                                int xf_next, int* flag) {
+  extern __shared__ float2 sm[];
+  const int row0 = blockIdx.x * R;
+  pdl_wait();
+  xi_rows<E, S, R, NT>(sm, w1, g, row0, twM, twP);
+  switch (mode) {
+    case LM_RK4_S0: xr_cells<LM_RK4_S0, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
+    case LM_RK4_S1: xr_cells<LM_RK4_S1, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
+    case LM_RK4_S2: xr_cells<LM_RK4_S2, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
+    default: xr_cells<LM_RK4_S3, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
+  }
+  if (!xf_next) return;
+  __syncthreads();  // the block's io.out rows are written; the c2r lines are read
+  xf_rows<E, S, R, NT, true>(sm, io.out, g, ms, ms_map, w1, row0, twM, twP);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,6 +394,29 @@ static mx_status run_xi(mx_ctx* ctx, float4* hd, cudaStream_t st, bool setup) {
   return launch_check("xi_kernel");
 }
 
+template <int E, int S, int R, int NT>
+static mx_status run_xr(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st, bool setup) {
+  const size_t sm = x_smem<E, S, R>();
+  if (setup) {
+    MX_CUDA_TRY(cudaFuncSetAttribute(xr_kernel<E, S, R, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+    MX_CUDA_TRY(cudaFuncSetAttribute(xr_kernel<E, S, R, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+    return MX_OK;
+  }
+  const Grid& g = ctx->g;
+  const int nrows = g.ny * g.nz;
+  const LocalCoef c = local_coef(ctx);
+  const dim3 grid((nrows + R - 1) / R);
+  if (c.dmi)
+    launch_pdl(xr_kernel<E, S, R, NT, true>, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map,
+               ctx->tw_m, ctx->tw_x, io, c, mode, xf_next ? 1 : 0, ctx->flag);
+  else
+    launch_pdl(xr_kernel<E, S, R, NT, false>, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map,
+               ctx->tw_m, ctx->tw_x, io, c, mode, xf_next ? 1 : 0, ctx->flag);
+  return launch_check("xr_kernel");
+}
+
 // x pass for M = Px/2 (returns MX_ERR_UNSUPPORTED when no specialisation fits).
 // Each size has a many-rows-per-block variant and a few-rows one; grids whose
 // row count would give fewer than two blocks per SM with the first take the
@@ -336,6 +442,30 @@ static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool invers
   return inverse ? run_xi<E, S, RS, NS>(ctx, hd, st, false) : run_xf<E, S, RS, NS>(ctx, m, st, false);
 }
 
+// The row kernel exists for the few-rows variant only (grids whose x passes
+// have fewer blocks than two per SM, where the step is bound by its kernel
+// boundaries); MX_ERR_UNSUPPORTED for the others.
+template <int E, int S, int RB, int RS>
+static mx_status xr_pass_rs(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st, bool setup) {
+  constexpr int NS = XfShape<S, RS>::NF > kFewRowsNT ? XfShape<S, RS>::NF : kFewRowsNT;
+  const int nrows = ctx->g.ny * ctx->g.nz;
+  if ((nrows + RB - 1) / RB >= kMinBlocks) return MX_ERR_UNSUPPORTED;
+  return run_xr<E, S, RS, NS>(ctx, mode, io, xf_next, st, setup);
+}
+
+static mx_status xr_pass(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st, bool setup) {
+  switch (ctx->g.Px / 2) {
+    case 1024: return xr_pass_rs<32, 32, 2, 1>(ctx, mode, io, xf_next, st, setup);
+    case 512: return xr_pass_rs<32, 16, 4, 1>(ctx, mode, io, xf_next, st, setup);
+    case 256: return xr_pass_rs<16, 16, 4, 1>(ctx, mode, io, xf_next, st, setup);
+    case 128: return xr_pass_rs<16, 8, 8, 2>(ctx, mode, io, xf_next, st, setup);
+    case 64: return xr_pass_rs<8, 8, 8, 2>(ctx, mode, io, xf_next, st, setup);
+    case 32: return xr_pass_rs<32, 1, 32, 4>(ctx, mode, io, xf_next, st, setup);
+    case 16: return xr_pass_rs<16, 1, 32, 4>(ctx, mode, io, xf_next, st, setup);
+    default: return MX_ERR_UNSUPPORTED;
+  }
+}
+
 static mx_status x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
   switch (ctx->g.Px / 2) {
     case 1024: return x_pass_rs<32, 32, 2, 1>(ctx, m, hd, inverse, st, setup);
@@ -355,8 +485,18 @@ mx_status fast_setup(mx_ctx* ctx) {
                 x_pass(ctx, nullptr, nullptr, false, nullptr, true) == MX_OK &&
                 x_pass(ctx, nullptr, nullptr, true, nullptr, true) == MX_OK;
   ctx->yz2d = ctx->fused_yz && ctx->g.Pz == 1 && yz2d_dispatch(ctx, nullptr, true) == MX_OK;
+  StageIO none{};
+  ctx->xrow = ctx->fast_x && xr_pass(ctx, LM_RK4_S0, none, false, nullptr, true) == MX_OK;
   clear_error();
   return MX_OK;
+}
+
+mx_status fast_row_stage(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st) {
+  if (mode < LM_RK4_S0 || mode > LM_RK4_S3) {
+    set_error("fast_row_stage: bad mode");
+    return MX_ERR_INVALID_ARG;
+  }
+  return xr_pass(ctx, mode, io, xf_next, st, false);
 }
 
 mx_status fast_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st) {

@@ -385,3 +385,31 @@ def test_fused_inverse_x_local_stage_bulk_workload():
         del ctx
     assert np.abs(out[0] - out[1]).max() <= 1e-6
     assert np.abs(np.linalg.norm(out[0], axis=-1) - 1).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["film17x9", "ragged37x21x5", "sheet30x40x1", "sheet24x300x1",
+                                  "line100x3x2", "wide600x24x2"])
+def test_row_kernel_rk4_matches_oracle(name):
+    """Few-row grids run each RK4 stage as the y/z passes plus one row kernel
+    (inverse x, local stage, the next stage's forward x): short trajectories
+    against the oracle and against the size-generic separate passes."""
+    from paper_2602_12242_gb300 import _lib
+    c = CASES[name]
+    m0 = f32(random_m(c, 29))
+    ctx = context(c)
+    assert ctx.kernel_name("x_inv_local") == "xr_kernel"
+    dt, n = 1e-14, 5
+    m = gpu_m(m0)
+    prof = ctx.profile_step(m, n, dt)
+    assert prof["x_inv_local"][1] == 4 * n and prof["x_fwd"][1] == n and "local_stage" not in prof
+    ctx.sync()
+    got = host(m)
+    ref = mm.run(problem(c), t64(m0), dt, n, "rk4").numpy()
+    assert np.abs(got - ref).max() <= 1e-4
+    assert np.abs(np.linalg.norm(got, axis=-1) - 1).max() <= 1e-6
+    gen = context(c, demag_path=_lib.MX_DEMAG_GENERIC)
+    assert gen.kernel_name("x_inv_local") == ""
+    m2 = gpu_m(m0)
+    gen.rk_step(m2, n, dt)
+    gen.sync()
+    assert np.abs(got - host(m2)).max() <= 1e-6
