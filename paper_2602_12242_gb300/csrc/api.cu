@@ -106,9 +106,24 @@ static std::vector<float2> twiddles32(int L) {
   return t;
 }
 
+// Whether an RK4 step runs as y/z passes plus one row kernel per stage.
+static bool row_steps(const mx_ctx* ctx, int method) {
+  return method == MX_RK4 && ctx->p.demag && ctx->xrow && !ctx->plane && !ctx->surrogate && !ctx->fno;
+}
+
+// The forward x pass of m into w1, which the first row-kernel step of a
+// sequence needs (each later step finds it left by the step before).
+static mx_status lead_x_pass(mx_ctx* ctx, const float4* m, cudaStream_t st) {
+  ProfScope ps(ctx, KID_X_FWD, st);
+  return fast_x_pass(ctx, m, nullptr, false, st);
+}
+
 // One time step on stream st.  m is the caller's field (step start, updated
-// in place).
-static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cudaStream_t st) {
+// in place).  With row kernels (row_steps), `lead` runs the forward x pass of
+// m first (else w1 must already hold it) and `tail` has the last stage leave
+// the forward x pass of the new m in w1 for a following step.
+static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cudaStream_t st, bool lead = true,
+                              bool tail = false) {
   if (method == MX_MRI) return mri_step(ctx, m, dt, st);
   const bool demag = ctx->p.demag != 0;
   float4* hd = demag ? ctx->hd : nullptr;
@@ -127,18 +142,15 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
   const float4* in[4] = {m, ctx->sa, ctx->sb, ctx->sa};
   float4* out[4] = {ctx->sa, ctx->sb, ctx->sa, m};
   const int modes[4] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3};
-  if (demag && ctx->xrow && !ctx->plane && !ctx->surrogate && !ctx->fno) {
-    // few-row grids: the forward x pass once, then per stage the y/z passes
-    // and one row kernel (inverse x, local stage, the next stage's forward x)
-    {
-      ProfScope ps(ctx, KID_X_FWD, st);
-      MX_TRY(fast_x_pass(ctx, m, nullptr, false, st));
-    }
+  if (row_steps(ctx, method)) {
+    // few-row grids: per stage the y/z passes and one row kernel (inverse x,
+    // local stage, the next stage's forward x)
+    if (lead) MX_TRY(lead_x_pass(ctx, m, st));
     for (int s = 0; s < 4; ++s) {
       StageIO io{in[s], nullptr, m, ctx->acc, out[s], (float)dt, MX_TERM_ALL};
       MX_TRY(demag_yz(ctx, st));
       ProfScope ps(ctx, KID_X_INV_LOCAL, st);
-      MX_TRY(fast_row_stage(ctx, modes[s], io, s < 3, st));
+      MX_TRY(fast_row_stage(ctx, modes[s], io, s < 3 || tail, st));
     }
     return MX_OK;
   }
@@ -487,7 +499,8 @@ mx_status mx_rk_step(mx_ctx* ctx, float* m, int nsteps, double dt, int method, m
     invalidate_graph(ctx);
     cudaGraph_t graph = nullptr;
     MX_CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-    mx_status s = enqueue_step(ctx, (float4*)m, dt, method, ctx->cap_stream);
+    // with row kernels the graph step starts from w1 and leaves it for the next
+    mx_status s = enqueue_step(ctx, (float4*)m, dt, method, ctx->cap_stream, false, true);
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
     if (s != MX_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -508,6 +521,7 @@ mx_status mx_rk_step(mx_ctx* ctx, float* m, int nsteps, double dt, int method, m
     ctx->graph_dt = dt;
     ctx->graph_method = method;
   }
+  if (row_steps(ctx, method)) MX_TRY(lead_x_pass(ctx, (const float4*)m, st));
   for (int s = 0; s < nsteps; ++s) MX_CUDA_TRY(cudaGraphLaunch(ctx->graph, st));
   return MX_OK;
 }
@@ -527,7 +541,7 @@ mx_status mx_profile_step(mx_ctx* ctx, float* m, int nsteps, double dt, int meth
   for (auto& e : prof.ev) MX_CUDA_TRY(cudaEventCreate(&e));
   ctx->prof = &prof;
   mx_status s = normalize_field(ctx, (float4*)m, st);
-  for (int q = 0; q < nsteps && s == MX_OK; ++q) s = enqueue_step(ctx, (float4*)m, dt, method, st);
+  for (int q = 0; q < nsteps && s == MX_OK; ++q) s = enqueue_step(ctx, (float4*)m, dt, method, st, q == 0, true);
   prof.harvest();
   ctx->prof = nullptr;
   for (auto& e : prof.ev) cudaEventDestroy(e);
