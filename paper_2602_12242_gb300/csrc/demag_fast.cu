@@ -59,7 +59,7 @@ __device__ __forceinline__ void xf_rows(float2* sm, const float4* __restrict__ m
   const int nrows = g.ny * g.nz;
   const int tid = threadIdx.x;
   // batches of kB cell pairs per thread: 2 kB independent loads in flight
-  constexpr int kB = 4;
+  constexpr int kB = (R * M + NT - 1) / NT < 4 ? (R * M + NT - 1) / NT : 4;
   for (int e0 = tid; e0 < R * M; e0 += NT * kB) {
     float4 a[kB], b[kB];
     float sa[kB], sb[kB];
@@ -98,7 +98,7 @@ __device__ __forceinline__ void xf_rows(float2* sm, const float4* __restrict__ m
   x_line_ffts<E, S, R, NT, false>(sm, twM);
   const long cs = (long)g.nz * g.ny * g.Hx;
   // batches of kB outputs per thread: the twiddle loads of a batch go out together
-  constexpr int kBo = 4;
+  constexpr int kBo = (3 * R * (M + 1) + NT - 1) / NT <= 9 ? (3 * R * (M + 1) + NT - 1) / NT : 4;
   for (int e0 = tid; e0 < 3 * R * (M + 1); e0 += NT * kBo) {
     float2 tw[kBo];
 #pragma unroll
@@ -151,7 +151,7 @@ __device__ __forceinline__ void xi_rows(float2* sm, const float2* __restrict__ w
   const int tid = threadIdx.x;
   const long cs = (long)g.nz * g.ny * g.Hx;
   // batches of kB elements per thread: 2 kB independent loads in flight
-  constexpr int kB = 4;
+  constexpr int kB = (3 * R * M + NT - 1) / NT <= 8 ? (3 * R * M + NT - 1) / NT : 4;
   for (int e0 = tid; e0 < 3 * R * M; e0 += NT * kB) {
     float2 A[kB], Bv[kB];
 #pragma unroll
@@ -218,13 +218,28 @@ __global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, G
 template <int MODE, bool DMI, int E, int S, int R, int NT>
 __device__ __forceinline__ void xr_cells(const float2* sm, const StageIO& io, const Grid& g, const LocalCoef& c,
                                          int row0, int* flag) {
+  // KC cells per thread and round with every cell's own loads issued first
+  constexpr int KC = (R * E * S + NT - 1) / NT < 3 ? (R * E * S + NT - 1) / NT : 3;
   const int nrows = g.ny * g.nz;
-  for (int e = threadIdx.x; e < R * g.nx; e += NT) {
-    const int r = e / g.nx, i = e - r * g.nx;
-    const int row = row0 + r;
-    if (row >= nrows) continue;
-    const int z = row / g.ny, y = row - z * g.ny;
-    local_cell_v<MODE, DMI>(io, g, c, i, y, z, (long)row * g.nx + i, xi_cell<E, S>(sm, r, i), flag);
+  const int total = min(R, nrows - row0) * g.nx;
+  for (int e0 = threadIdx.x; e0 < total; e0 += KC * NT) {
+    CellIn v[KC];
+    long idx[KC];
+#pragma unroll
+    for (int u = 0; u < KC; ++u) {
+      const int e = min(e0 + u * NT, total - 1);
+      idx[u] = (long)row0 * g.nx + e;
+      v[u] = load_cell<MODE>(io, c, idx[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < KC; ++u) {
+      const int e = e0 + u * NT;
+      if (e >= total) break;
+      const int r = e / g.nx, i = e - r * g.nx;
+      const int row = row0 + r;
+      const int z = row / g.ny, y = row - z * g.ny;
+      local_cell_in<MODE, DMI>(io, g, c, i, y, z, idx[u], xi_cell<E, S>(sm, r, i), v[u], flag);
+    }
   }
 }
 
@@ -276,6 +291,25 @@ __global__ void __launch_bounds__(NT) yz2d_kernel(float2* __restrict__ w1, Grid 
     twS[q] = __ldg(&twH[(q % S) * (q / S)]);
     twS2[q] = __ldg(&twPy[q]);
   }
+  // this thread's tensor entries for the multiply below (constants, so read
+  // while the previous kernel may still run)
+  constexpr int NMUL = T * 2 * LH, KM = (NMUL + NT - 1) / NT;
+  const long no = (long)g.Hx * g.Oy * g.Oz;
+  float4 nt[KM];
+#pragma unroll
+  for (int u = 0; u < KM; ++u) {
+    const int e = tid + u * NT;
+    const int j = e % LH, h = (e / LH) % 2, t = e / (2 * LH);
+    const int kx = kx0 + t;
+    nt[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < NMUL && kx < g.Hx) {
+      const int ky = 2 * j + h;
+      const bool fy = ky > (g.Py >> 1);
+      const long o = (long)(fy ? g.Py - ky : ky) * g.Hx + kx;
+      nt[u] = make_float4(__ldg(&nhat[o]), __ldg(&nhat[no + o]), __ldg(&nhat[2 * no + o]),
+                          (fy ? -1.f : 1.f) * __ldg(&nhat[3 * no + o]));
+    }
+  }
   pdl_wait();  // the tables are constants; w1 is the previous kernel's
   __syncthreads();
   // line (c, t, h) at ((c T + t) 2 + h) PITCH; every load of a thread in flight at once
@@ -302,16 +336,13 @@ __global__ void __launch_bounds__(NT) yz2d_kernel(float2* __restrict__ w1, Grid 
   __syncthreads();
   if (tid < NF) line_fft<E, S, false, true, true>(sm + (tid / S) * PITCH, tid % S, twS);
   __syncthreads();
-  const long no = (long)g.Hx * g.Oy * g.Oz;
-  for (int e = tid; e < T * 2 * LH; e += NT) {
+#pragma unroll
+  for (int u = 0; u < KM; ++u) {
+    const int e = tid + u * NT;
     const int j = e % LH, h = (e / LH) % 2, t = e / (2 * LH);
     const int kx = kx0 + t;
-    if (kx >= g.Hx) continue;
-    const int ky = 2 * j + h;
-    const bool fy = ky > (g.Py >> 1);
-    const long o = (long)(fy ? g.Py - ky : ky) * g.Hx + kx;
-    const float nxx = __ldg(&nhat[o]), nyy = __ldg(&nhat[no + o]), nzz = __ldg(&nhat[2 * no + o]);
-    const float nxy = (fy ? -1.f : 1.f) * __ldg(&nhat[3 * no + o]);
+    if (e >= NMUL || kx >= g.Hx) continue;
+    const float nxx = nt[u].x, nyy = nt[u].y, nzz = nt[u].z, nxy = nt[u].w;
     float2* px = sm + ((0 * T + t) * 2 + h) * PITCH + j;
     float2* py = sm + ((1 * T + t) * 2 + h) * PITCH + j;
     float2* pz = sm + ((2 * T + t) * 2 + h) * PITCH + j;
