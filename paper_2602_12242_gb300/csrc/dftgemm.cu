@@ -1,5 +1,6 @@
 // Split-BF16 DFT-as-GEMM first radix stage of the x transforms (precision
-// option MX_FFT_SPLIT_BF16 of the per-kx-plane demag path).
+// option MX_FFT_SPLIT_BF16 of the per-kx-plane demag path), on the tcgen05
+// tensor cores with the accumulator in tensor memory.
 //
 // A line of M = 32 S points is transformed in two steps (regfft.cuh): 32-point
 // DFTs over the stride-S subsequences x[s + S n], twiddles W_M^(s k1), then
@@ -20,110 +21,132 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "bulk.cuh"
 #include "mma.cuh"
 #include "regfft.cuh"
+#include "tc05.cuh"
 
 namespace mx {
 
-constexpr int kDftPitch = 72;  // bf16 elements per row of the A and X tiles (64 + 8 pad)
+// Operands in the canonical K-major layout without swizzle (tc05.cuh): the
+// element (row, k) of a 16-bit matrix with 64 columns of K sits at byte
+// (row / 8) * 1024 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, so core
+// matrices adjacent along K are 128 bytes apart (LBO) and 8-row groups 1024
+// bytes apart (SBO).
+__host__ __device__ constexpr uint32_t dft_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
 
-// The block's V = 192 subsequences: line l = v / S, s = v % S.
+// The block's V = 192 subsequences: line l = v / S, s = v % S.  On the tensor
+// cores the GEMM is D (V x 64) = X (V x 64) F^T, vectors along M in two
+// 128-row tiles (rows 192..255 of the second are scratch), F (64 x 64) the
+// B operand; D lives in tensor memory, 64 FP32 columns per tile.
 template <int S> struct DftShape {
   static constexpr int E = 32;
   static constexpr int M = E * S;
   static constexpr int R = 64 / S;          // rows per block (3R lines, 3RS = 192 vectors)
   static constexpr int NT = 3 * R * S;      // threads
   static constexpr int V = 3 * R * S;       // vectors
+  static constexpr int VP = 256;            // vectors padded to two M = 128 tiles
   static constexpr int P = LineFft<E, S>::kPitch + 1;
   static constexpr size_t smem_lines = sizeof(float2) * 3 * R * P;
-  static constexpr size_t smem_a = sizeof(bf16_t) * 2 * 64 * kDftPitch;
-  static constexpr size_t smem_x = sizeof(bf16_t) * 2 * V * kDftPitch;
+  static constexpr size_t smem_a = 2 * 64 * 64 * 2;      // F hi, lo
+  static constexpr size_t smem_x = 2 * VP * 64 * 2;      // X hi, lo
   static constexpr size_t smem = smem_lines + smem_a + smem_x;
+  static_assert(V == 192 && NT == 192 && smem_lines % 16 == 0, "DFT stage shape");
 };
 
 // Step 1 by split-BF16 GEMM on the block's lines; writes the twiddled rows
-// k1 * (S + 1) + s that line_fft_step2 reads.  A (hi, lo) for the direction is
-// in global memory: 2 x [64][64] bf16.
+// k1 * (S + 1) + s that line_fft_step2 reads.  F (hi, lo) for the direction
+// is in global memory: 2 x [64][64] bf16, row = output (Re k, Im k), column
+// = input (Re n, Im n).  sa, sx: 16-byte aligned shared buffers; bar, tb:
+// the block's mbarrier and tensor-memory base (128 columns, allocated by the
+// caller); flag receives kFlagTimeout if the MMAs do not complete in time.
 template <int S, bool INV>
-__device__ __forceinline__ void dft_stage1(float2* lines, bf16_t* sa, bf16_t* sx, const bf16_t* __restrict__ agl,
-                                           const float2* __restrict__ twM) {
+__device__ __forceinline__ void dft_stage1(float2* lines, unsigned char* sa, unsigned char* sx,
+                                           const bf16_t* __restrict__ agl, const float2* __restrict__ twM,
+                                           uint64_t* bar, uint32_t tb, int* flag) {
   typedef DftShape<S> D;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // A hi/lo into shared memory
+  // F hi/lo into shared memory: 16-byte chunk (part, row, ch) = 8 consecutive k
   for (int e = tid; e < 2 * 64 * 8; e += D::NT) {
     const int part = e / (64 * 8), row = (e / 8) % 64, ch = e % 8;
-    cp_async16(smem_u32(sa + (part * 64 + row) * kDftPitch + ch * 8), agl + (part * 64 + row) * 64 + ch * 8, true);
+    cp_async16(smem_u32(sa + part * 8192 + dft_off(row, 8 * ch)), agl + (part * 64 + row) * 64 + ch * 8, true);
   }
-  // X hi/lo: vector v, k = n (re) and 32 + n (im)
-  bf16_t* xh = sx;
-  bf16_t* xl = sx + D::V * kDftPitch;
-  for (int e = tid; e < D::V * 32; e += D::NT) {
-    const int v = e % D::V, n = e / D::V;
+  // X hi/lo: vector v, k = n (re) and 32 + n (im); a work item is 8
+  // consecutive n of one vector, stored as four 16-byte rows of core matrices
+  unsigned char* xh = sx;
+  unsigned char* xl = sx + D::VP * 128;
+  for (int e = tid; e < D::V * 4; e += D::NT) {
+    const int v = e % D::V, c = e / D::V;
     const int l = v / S, s = v % S;
-    const float2 x = lines[l * D::P + s + S * n];
-    const bf16_t rh = f2bf(x.x), ih = f2bf(x.y);
-    xh[v * kDftPitch + n] = rh;
-    xh[v * kDftPitch + 32 + n] = ih;
-    xl[v * kDftPitch + n] = f2bf(x.x - bf2f(rh));
-    xl[v * kDftPitch + 32 + n] = f2bf(x.y - bf2f(ih));
+    const float2* src = lines + l * D::P + s + S * 8 * c;
+    uint32_t rh[4], ih[4], rl[4], il[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 x0 = src[S * (2 * q)], x1 = src[S * (2 * q + 1)];
+      const bf16_t r0 = f2bf(x0.x), r1 = f2bf(x1.x), i0 = f2bf(x0.y), i1 = f2bf(x1.y);
+      rh[q] = (uint32_t)r0 | ((uint32_t)r1 << 16);
+      ih[q] = (uint32_t)i0 | ((uint32_t)i1 << 16);
+      rl[q] = pack2(x0.x - bf2f(r0), x1.x - bf2f(r1));
+      il[q] = pack2(x0.y - bf2f(i0), x1.y - bf2f(i1));
+    }
+    *(uint4*)(xh + dft_off(v, 8 * c)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+    *(uint4*)(xh + dft_off(v, 32 + 8 * c)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+    *(uint4*)(xl + dft_off(v, 8 * c)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+    *(uint4*)(xl + dft_off(v, 32 + 8 * c)) = make_uint4(il[0], il[1], il[2], il[3]);
   }
   cp_async_wait_all();
+  fence_proxy_async_smem();  // the operands are read by the tensor core (async proxy)
+  tc_fence_before_sync();
   __syncthreads();
-  // warp w: vectors [32 w, 32 w + 32) = 4 n tiles, all 4 m tiles
-  float acc[4][4][4];
+  if (tid == 0) {
+    tc_fence_after_sync();
+    constexpr uint32_t idesc = tc_idesc_bf16(128, 64);
+    const uint32_t a0 = smem_u32(sa), x0 = smem_u32(sx);
 #pragma unroll
-  for (int mt = 0; mt < 4; ++mt)
+    for (int t = 0; t < 2; ++t) {
+      // hi.hi, lo.hi (X part), hi.lo (F part)
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
-  const bf16_t* ah = sa;
-  const bf16_t* al = sa + 64 * kDftPitch;
+      for (int pr = 0; pr < 3; ++pr) {
+        const uint32_t xb = x0 + (pr == 1 ? D::VP * 128 : 0) + t * 128 * 128;
+        const uint32_t fb = a0 + (pr == 2 ? 8192 : 0);
 #pragma unroll
-  for (int ks = 0; ks < 4; ++ks) {
-    uint32_t bh[4][2], bl[4][2];
-#pragma unroll
-    for (int np = 0; np < 2; ++np) {
-      const int vrow = warp * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3);
-      const int kof = ks * 16 + ((lane >> 3) & 1) * 8;
-      ldsm_x4(smem_u32(xh + vrow * kDftPitch + kof), bh[2 * np][0], bh[2 * np][1], bh[2 * np + 1][0],
-              bh[2 * np + 1][1]);
-      ldsm_x4(smem_u32(xl + vrow * kDftPitch + kof), bl[2 * np][0], bl[2 * np][1], bl[2 * np + 1][0],
-              bl[2 * np + 1][1]);
-    }
-#pragma unroll
-    for (int mt = 0; mt < 4; ++mt) {
-      const int arow = mt * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;
-      const int akof = ks * 16 + (lane >> 4) * 8;
-      uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
-      ldsm_x4(smem_u32(ah + arow * kDftPitch + akof), h0, h1, h2, h3);
-      ldsm_x4(smem_u32(al + arow * kDftPitch + akof), l0, l1, l2, l3);
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        mma16816(acc[mt][nt], h0, h1, h2, h3, bh[nt][0], bh[nt][1]);
-        mma16816(acc[mt][nt], h0, h1, h2, h3, bl[nt][0], bl[nt][1]);
-        mma16816(acc[mt][nt], l0, l1, l2, l3, bh[nt][0], bh[nt][1]);
+        for (int ks = 0; ks < 4; ++ks)
+          tc_mma_bf16(tb + t * 64, tc_sdesc(xb + ks * 256, 128, 1024), tc_sdesc(fb + ks * 256, 128, 1024), idesc,
+                      pr > 0 || ks > 0);
       }
+    }
+    tc_commit(bar);
+  }
+  if (!mbar_wait(bar, 0)) atomicOr(flag, kFlagTimeout);
+  tc_fence_after_sync();
+  // row v of D: tile warp / 4, lanes of this warp's quarter; 64 columns =
+  // (Re k1, Im k1) for k1 < 32.  The lines' inputs were copied into X above.
+  const int t = warp >> 2;
+  const int v = t * 128 + 32 * (warp & 3) + lane;
+  float d[64];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float q[8];
+    tmem_ld8(tb + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(t * 64 + 8 * j), q);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[8 * j + i] = q[i];
+  }
+  if (v < D::V) {
+    const int l = v / S, s = v % S;
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) {
+      float2 y = make_float2(d[k1], d[32 + k1]);
+      if (k1 > 0) {
+        float2 w = __ldg(&twM[s * k1]);
+        if (INV) w.y = -w.y;
+        y = cmul(y, w);
+      }
+      lines[l * D::P + k1 * (S + 1) + s] = y;
     }
   }
-  __syncthreads();  // every thread has read its line inputs from X (copied); lines may be overwritten
-  // rows 16 mt + g (+8): k1 (mt 0, 1 real; mt 2, 3 imaginary), cols: vectors
-  const int g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int k1 = mt * 16 + g + (r >= 2 ? 8 : 0);
-        const int v = warp * 32 + nt * 8 + 2 * q + (r & 1);
-        const int l = v / S, s = v % S;
-        float2 y = make_float2(acc[mt][nt][r], acc[mt + 2][nt][r]);
-        if (k1 > 0) {
-          float2 w = __ldg(&twM[s * k1]);
-          if (INV) w.y = -w.y;
-          y = cmul(y, w);
-        }
-        lines[l * D::P + k1 * (S + 1) + s] = y;
-      }
+  tc_fence_before_sync();
   __syncthreads();
 }
 
@@ -132,13 +155,18 @@ __global__ void __launch_bounds__(DftShape<S>::NT) xfk_dft_kernel(const float4* 
                                                                   const float* __restrict__ ms_map,
                                                                   float2* __restrict__ w1, const bf16_t* __restrict__ agl,
                                                                   const float2* __restrict__ twM,
-                                                                  const float2* __restrict__ twP) {
+                                                                  const float2* __restrict__ twP, int* flag) {
   typedef DftShape<S> D;
   constexpr int M = D::M, P = D::P, R = D::R, NT = D::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
   float2* sm = (float2*)smraw;
-  bf16_t* sa = (bf16_t*)(smraw + D::smem_lines);
-  bf16_t* sx = (bf16_t*)(smraw + D::smem_lines + D::smem_a);
+  unsigned char* sa = smraw + D::smem_lines;
+  unsigned char* sx = smraw + D::smem_lines + D::smem_a;
+  if (threadIdx.x < 32) tmem_alloc(&tbase, 128);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  pdl_wait();
   const int ychunks = (g.ny + R - 1) / R;
   const int z = blockIdx.x / ychunks;
   const int y0 = (blockIdx.x % ychunks) * R;
@@ -165,8 +193,15 @@ __global__ void __launch_bounds__(DftShape<S>::NT) xfk_dft_kernel(const float4* 
     sm[(3 * r + 1) * P + n] = zy;
     sm[(3 * r + 2) * P + n] = zz;
   }
+  tc_fence_before_sync();
   __syncthreads();
-  dft_stage1<S, false>(sm, sa, sx, agl, twM);
+  tc_fence_after_sync();
+  const uint32_t tb = tbase;
+  dft_stage1<S, false>(sm, sa, sx, agl, twM, &bar, tb, flag);
+  if (threadIdx.x < 32) {
+    tc_fence_after_sync();
+    tmem_dealloc(tb, 128);
+  }
   line_fft_step2<32, S, false>(sm + (tid / S) * P, tid % S);
   __syncthreads();
   const long plane = 3L * g.nz * g.ny;
@@ -190,13 +225,18 @@ template <int S>
 __global__ void __launch_bounds__(DftShape<S>::NT) xik_dft_kernel(const float2* __restrict__ w2, Grid g,
                                                                   float4* __restrict__ hd, const bf16_t* __restrict__ agl,
                                                                   const float2* __restrict__ twM,
-                                                                  const float2* __restrict__ twP) {
+                                                                  const float2* __restrict__ twP, int* flag) {
   typedef DftShape<S> D;
   constexpr int M = D::M, P = D::P, R = D::R, NT = D::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
   float2* sm = (float2*)smraw;
-  bf16_t* sa = (bf16_t*)(smraw + D::smem_lines);
-  bf16_t* sx = (bf16_t*)(smraw + D::smem_lines + D::smem_a);
+  unsigned char* sa = smraw + D::smem_lines;
+  unsigned char* sx = smraw + D::smem_lines + D::smem_a;
+  if (threadIdx.x < 32) tmem_alloc(&tbase, 128);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  pdl_wait();
   const int ychunks = (g.ny + R - 1) / R;
   const int z = blockIdx.x / ychunks;
   const int y0 = (blockIdx.x % ychunks) * R;
@@ -218,8 +258,15 @@ __global__ void __launch_bounds__(DftShape<S>::NT) xik_dft_kernel(const float2* 
     }
     sm[(3 * r + c) * P + k] = v;
   }
+  tc_fence_before_sync();
   __syncthreads();
-  dft_stage1<S, true>(sm, sa, sx, agl + 2 * 64 * 64, twM);
+  tc_fence_after_sync();
+  const uint32_t tb = tbase;
+  dft_stage1<S, true>(sm, sa, sx, agl + 2 * 64 * 64, twM, &bar, tb, flag);
+  if (threadIdx.x < 32) {
+    tc_fence_after_sync();
+    tmem_dealloc(tb, 128);
+  }
   line_fft_step2<32, S, true>(sm + (tid / S) * P, tid % S);
   __syncthreads();
   for (int e = tid; e < R * g.nx; e += NT) {
@@ -294,11 +341,12 @@ static mx_status dft_run(mx_ctx* ctx, const float4* m, float4* hd, bool inverse,
   const int nblk = g.nz * ((g.ny + D::R - 1) / D::R);
   const bf16_t* A = (const bf16_t*)ctx->dft_a;
   if (!inverse) {
-    xfk_dft_kernel<S><<<nblk, D::NT, D::smem, st>>>(m, g, (float)ctx->p.Ms, ctx->ms_map, ctx->w1, A, ctx->tw_m,
-                                                    ctx->tw_x);
+    launch_pdl(xfk_dft_kernel<S>, dim3(nblk), dim3(D::NT), D::smem, st, m, g, (float)ctx->p.Ms, ctx->ms_map,
+               ctx->w1, A, ctx->tw_m, ctx->tw_x, ctx->flag);
     return launch_check("xfk_dft_kernel");
   }
-  xik_dft_kernel<S><<<nblk, D::NT, D::smem, st>>>(ctx->w2, g, hd, A, ctx->tw_m, ctx->tw_x);
+  launch_pdl(xik_dft_kernel<S>, dim3(nblk), dim3(D::NT), D::smem, st, ctx->w2, g, hd, A, ctx->tw_m, ctx->tw_x,
+             ctx->flag);
   return launch_check("xik_dft_kernel");
 }
 
