@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "local.cuh"
+#include "xrows.cuh"
 
 namespace mx {
 
@@ -95,11 +96,11 @@ __device__ __forceinline__ void prep_cell(const float4* __restrict__ m, const fl
 // w); the Ms gradient term; the stage's share of lam_acc; returns the next
 // stage rate's cotangent (STAGE 3, 2, 1) or zero (STAGE 0).
 template <bool DMI, int STAGE>
-__device__ __forceinline__ float3 finish_cell(const float4* __restrict__ m, const float4* __restrict__ wbuf,
-                                              const float4* __restrict__ hdw, const float4* __restrict__ gm,
-                                              const float4* __restrict__ lam_u4, float4* __restrict__ lam_acc,
-                                              double* __restrict__ dms, const Grid& g, const LocalCoef& c, float dt,
-                                              int i, int j, int k, long idx) {
+__device__ __forceinline__ float3 finish_cell_v(const float4* __restrict__ m, const float4* __restrict__ wbuf,
+                                                float3 hdwv, const float4* __restrict__ gm,
+                                                const float4* __restrict__ lam_u4, float4* __restrict__ lam_acc,
+                                                double* __restrict__ dms, const Grid& g, const LocalCoef& c, float dt,
+                                                int i, int j, int k, long idx) {
   const float ms = c.ms_map ? __ldg(&c.ms_map[idx]) : c.Ms;
   const float inv_ms = 1.f / ms;
   // L applied to w = g_H / Ms: demag from the convolution, local terms here
@@ -107,7 +108,7 @@ __device__ __forceinline__ float3 finish_cell(const float4* __restrict__ m, cons
   cl.hx = cl.hy = cl.hz = 0.f;  // the bias is not part of the linear operator
   const float3 wc = f3(wbuf[idx]);
   Terms tw;
-  local_terms<DMI>(wbuf, hdw, g, cl, i, j, k, idx, wc, inv_ms, tw);
+  local_terms_v<DMI>(wbuf, hdwv, g, cl, i, j, k, idx, wc, inv_ms, tw);
   const float3 Lw = tw.demag + tw.exch + tw.anis + tw.dmi;
   const float4 m4 = m[idx];
   const float3 mc = f3(m4);
@@ -132,6 +133,17 @@ __device__ __forceinline__ float3 finish_cell(const float4* __restrict__ m, cons
   const float cu4 = (STAGE == 1) ? dt / 6.f : dt / 3.f;
   const float cus = (STAGE == 3) ? dt : 0.5f * dt;
   return cu4 * u4 + cus * lu;
+}
+
+// The same with the demag field of w read from hdw (zero if hdw is null).
+template <bool DMI, int STAGE>
+__device__ __forceinline__ float3 finish_cell(const float4* __restrict__ m, const float4* __restrict__ wbuf,
+                                              const float4* __restrict__ hdw, const float4* __restrict__ gm,
+                                              const float4* __restrict__ lam_u4, float4* __restrict__ lam_acc,
+                                              double* __restrict__ dms, const Grid& g, const LocalCoef& c, float dt,
+                                              int i, int j, int k, long idx) {
+  return finish_cell_v<DMI, STAGE>(m, wbuf, hdw ? f3(__ldg(&hdw[idx])) : make_float3(0.f, 0.f, 0.f), gm, lam_u4,
+                                   lam_acc, dms, g, c, dt, i, j, k, idx);
 }
 
 template <bool DMI>
@@ -204,6 +216,125 @@ __global__ void __launch_bounds__(256) adj_finish_prep_kernel(
   prep_cell<DMI>(m_prev, hd_prev, g, c, i, j, k, idx, nk, wbuf_out, gm_out);
 }
 
+// ---------------------------------------------------------------------------
+// Row kernels of the reverse sweep on few-row grids (as the forward step's
+// row kernels): per stage, the y/z passes of w's spectrum and one kernel that
+// takes the c2r transforms of its block's rows (the demag field of w, kept in
+// shared memory), finishes the stage and prepares the one before at every
+// cell of those rows, and leaves the forward x pass of the new w in w1.  The
+// new w and g_m go to the other buffer pair, and the block reads its own rows
+// of the new w back after a block barrier.
+// ---------------------------------------------------------------------------
+struct AdjRowArgs {
+  const float4* mnew;     // step result (begin only)
+  const float4* m;        // state of the stage being finished
+  const float4* wbuf;     // its w (stencil) and g_m
+  const float4* gm;
+  float4* lam_u4;
+  float4* lam_acc;
+  double* dms;
+  const float4* m_prev;   // state and demag field of the stage being prepared
+  const float4* hd_prev;
+  float4* wbuf_out;       // its w and g_m
+  float4* gm_out;
+};
+
+template <bool DMI, int R, int NT>
+__device__ __forceinline__ void adj_row_begin_cells(const AdjRowArgs& a, const Grid& g, const LocalCoef& c, float dt,
+                                                    int row0) {
+  const int total = min(R, g.ny * g.nz - row0) * g.nx;
+  for (int e = threadIdx.x; e < total; e += NT) {
+    const int r = e / g.nx, i = e - r * g.nx;
+    const int row = row0 + r;
+    const int z = row / g.ny, y = row - z * g.ny;
+    const long idx = (long)row * g.nx + i;
+    const float4 n4 = a.mnew[idx];
+    const float3 nc = f3(n4);
+    const float3 l = f3(a.lam_acc[idx]);
+    const float3 lu = (1.f / n4.w) * (l - dot3(nc, l) * nc);
+    a.lam_u4[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+    a.lam_acc[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+    prep_cell<DMI>(a.m_prev, a.hd_prev, g, c, i, y, z, idx, (dt / 6.f) * lu, a.wbuf_out, a.gm_out);
+  }
+}
+
+template <bool DMI, int STAGE, int E, int S, int R, int NT>
+__device__ __forceinline__ void adj_row_cells(const float2* sm, const AdjRowArgs& a, const Grid& g,
+                                              const LocalCoef& c, float dt, int row0) {
+  const int total = min(R, g.ny * g.nz - row0) * g.nx;
+  for (int e = threadIdx.x; e < total; e += NT) {
+    const int r = e / g.nx, i = e - r * g.nx;
+    const int row = row0 + r;
+    const int z = row / g.ny, y = row - z * g.ny;
+    const long idx = (long)row * g.nx + i;
+    const float3 nk = finish_cell_v<DMI, STAGE>(a.m, a.wbuf, xi_cell<E, S>(sm, r, i), a.gm, a.lam_u4, a.lam_acc,
+                                                a.dms, g, c, dt, i, y, z, idx);
+    if (STAGE > 0) prep_cell<DMI>(a.m_prev, a.hd_prev, g, c, i, y, z, idx, nk, a.wbuf_out, a.gm_out);
+  }
+}
+
+template <int E, int S, int R, int NT, bool DMI>
+__global__ void __launch_bounds__(NT) adj_row_begin_kernel(float2* __restrict__ w1, Grid g, float ms,
+                                                           const float* __restrict__ ms_map,
+                                                           const float2* __restrict__ twM,
+                                                           const float2* __restrict__ twP, AdjRowArgs a, LocalCoef c,
+                                                           float dt) {
+  extern __shared__ float2 sm[];
+  const int row0 = blockIdx.x * R;
+  pdl_wait();
+  adj_row_begin_cells<DMI, R, NT>(a, g, c, dt, row0);
+  __syncthreads();
+  xf_rows<E, S, R, NT, true>(sm, a.wbuf_out, g, ms, ms_map, w1, row0, twM, twP);
+}
+
+template <int E, int S, int R, int NT, bool DMI>
+__global__ void __launch_bounds__(NT) adj_row_kernel(float2* __restrict__ w1, Grid g, float ms,
+                                                     const float* __restrict__ ms_map, const float2* __restrict__ twM,
+                                                     const float2* __restrict__ twP, AdjRowArgs a, LocalCoef c,
+                                                     float dt, int stage) {
+  extern __shared__ float2 sm[];
+  const int row0 = blockIdx.x * R;
+  pdl_wait();
+  xi_rows<E, S, R, NT>(sm, w1, g, row0, twM, twP);
+  switch (stage) {
+    case 3: adj_row_cells<DMI, 3, E, S, R, NT>(sm, a, g, c, dt, row0); break;
+    case 2: adj_row_cells<DMI, 2, E, S, R, NT>(sm, a, g, c, dt, row0); break;
+    case 1: adj_row_cells<DMI, 1, E, S, R, NT>(sm, a, g, c, dt, row0); break;
+    default: adj_row_cells<DMI, 0, E, S, R, NT>(sm, a, g, c, dt, row0); return;
+  }
+  __syncthreads();  // the block's rows of the new w are written; the c2r lines are read
+  xf_rows<E, S, R, NT, true>(sm, a.wbuf_out, g, ms, ms_map, w1, row0, twM, twP);
+}
+
+// Launches the begin kernel (begin) or the stage kernel of `stage` for the
+// grid's few-row x configuration.
+struct AdjRowLaunch {
+  mx_ctx* ctx;
+  const AdjRowArgs* a;
+  float dt;
+  int stage;
+  bool begin;
+  cudaStream_t st;
+  template <int E, int S, int R, int NT> mx_status run() {
+    const size_t sm = sizeof(float2) * XfShape<S, R>::lines * LineFft<E, S>::kPitch;
+    static_assert(sizeof(float2) * XfShape<S, R>::lines * LineFft<E, S>::kPitch <= 48 * 1024,
+                  "row kernel shared memory");
+    const Grid& g = ctx->g;
+    const LocalCoef c = local_coef(ctx);
+    const dim3 grid((g.ny * g.nz + R - 1) / R);
+    if (begin) {
+      auto k = c.dmi ? adj_row_begin_kernel<E, S, R, NT, true> : adj_row_begin_kernel<E, S, R, NT, false>;
+      launch_pdl(k, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map, ctx->tw_m, ctx->tw_x, *a,
+                 c, dt);
+      return launch_check("adj_row_begin_kernel");
+    }
+    auto k = c.dmi ? adj_row_kernel<E, S, R, NT, true> : adj_row_kernel<E, S, R, NT, false>;
+    launch_pdl(k, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map, ctx->tw_m, ctx->tw_x, *a, c,
+               dt, stage);
+    return launch_check("adj_row_kernel");
+  }
+};
+
 // lam_u4 = J_N(u4)^T lam (m_new carries |u4| in w); lam_acc = lam_u4; lam_k = dt/6 lam_u4
 __global__ void adj_begin_kernel(const float4* __restrict__ mnew, float4* __restrict__ lam_acc,
                                  float4* __restrict__ lam_u4, float4* __restrict__ lam_k, long n, float dt) {
@@ -272,6 +403,9 @@ mx_status adjoint_reserve(mx_ctx* ctx, int nsteps, int every) {
     return MX_ERR_INVALID_ARG;
   }
   adjoint_free(ctx);
+  // this unit's copy of the W_32 table used by the register FFTs of the
+  // reverse sweep's row kernels
+  MX_TRY(upload_w32());
   AdjWork* w = new AdjWork();
   ctx->adj = w;
   w->nsteps = nsteps;
@@ -341,6 +475,9 @@ static bool graphs_usable(const mx_ctx* ctx) { return ctx->prof == nullptr; }
 // Stored segments.  Step i of the segment takes seg[i] to seg[i + 1]; its
 // stage states are segst[i][0..2] and the demag fields of seg[i] and the
 // three stage states seghd[i][0..3].
+// With row kernels (row_steps) each stage is the y/z passes plus one row
+// kernel that also writes the stage state's demag field; step i = 0 runs the
+// forward x pass of seg[0] first, and each step leaves that of seg[i + 1].
 static mx_status stored_recompute_step(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, cudaStream_t st) {
   const long nc = ctx->g.ncell;
   const float4* m = w->seg + (long)i * nc;
@@ -349,6 +486,15 @@ static mx_status stored_recompute_step(mx_ctx* ctx, AdjWork* w, int i, float dt,
   const float4* states[4] = {m, S, S + nc, S + 2 * nc};
   float4* outs[4] = {S, S + nc, S + 2 * nc, w->seg + (long)(i + 1) * nc};
   const int modes[4] = {LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3};
+  if (demag && row_steps(ctx, MX_RK4)) {
+    if (i == 0) MX_TRY(fast_x_pass(ctx, m, nullptr, false, st));
+    for (int q = 0; q < 4; ++q) {
+      StageIO io{states[q], nullptr, m, ctx->acc, outs[q], dt, MX_TERM_ALL};
+      MX_TRY(demag_yz(ctx, st));
+      MX_TRY(fast_row_stage(ctx, modes[q], io, true, Hd + q * nc, st));
+    }
+    return MX_OK;
+  }
   for (int q = 0; q < 4; ++q) {
     if (demag) MX_TRY(demag_field(ctx, states[q], Hd + q * nc, st));
     StageIO io{states[q], demag ? Hd + q * nc : nullptr, m, ctx->acc, outs[q], dt, MX_TERM_ALL};
@@ -427,6 +573,28 @@ static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt,
   // demag fields of the stage states are zero without demag (hd4 cleared)
   const float4* hd[4];
   for (int q = 0; q < 4; ++q) hd[q] = demag ? Hd + q * nc : w->hd4;
+  if (demag && row_steps(ctx, MX_RK4)) {
+    // row kernels: begin + prep of stage 3, then per stage the y/z passes of
+    // w's spectrum and the finish (+ prep of the stage before) row kernel
+    AdjRowArgs a{mnew, nullptr, nullptr, nullptr, w->lam_u4, w->lam_acc, w->dms, states[3], hd[3], wb[0], gmb[0]};
+    AdjRowLaunch L{ctx, &a, dt, 0, true, st};
+    MX_TRY(few_rows_dispatch(g.Px / 2, L));
+    int b = 0;
+    for (int q = 3; q >= 0; --q) {
+      MX_TRY(demag_yz(ctx, st));
+      a.m = states[q];
+      a.wbuf = wb[b];
+      a.gm = gmb[b];
+      a.m_prev = q > 0 ? states[q - 1] : nullptr;
+      a.hd_prev = q > 0 ? hd[q - 1] : nullptr;
+      a.wbuf_out = wb[b ^ 1];
+      a.gm_out = gmb[b ^ 1];
+      AdjRowLaunch Lq{ctx, &a, dt, q, false, st};
+      MX_TRY(few_rows_dispatch(g.Px / 2, Lq));
+      b ^= 1;
+    }
+    return MX_OK;
+  }
   adj_begin_prep_kernel<DMI><<<grid, block, 0, st>>>(mnew, states[3], hd[3], w->lam_acc, w->lam_u4, wb[0], gmb[0],
                                                      g, c, dt);
   MX_TRY(launch_check("adj_begin_prep_kernel"));

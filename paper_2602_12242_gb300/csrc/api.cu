@@ -107,7 +107,7 @@ static std::vector<float2> twiddles32(int L) {
 }
 
 // Whether an RK4 step runs as y/z passes plus one row kernel per stage.
-static bool row_steps(const mx_ctx* ctx, int method) {
+bool row_steps(const mx_ctx* ctx, int method) {
   return method == MX_RK4 && ctx->p.demag && ctx->xrow && !ctx->plane && !ctx->surrogate && !ctx->fno;
 }
 
@@ -150,7 +150,7 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
       StageIO io{in[s], nullptr, m, ctx->acc, out[s], (float)dt, MX_TERM_ALL};
       MX_TRY(demag_yz(ctx, st));
       ProfScope ps(ctx, KID_X_INV_LOCAL, st);
-      MX_TRY(fast_row_stage(ctx, modes[s], io, s < 3 || tail, st));
+      MX_TRY(fast_row_stage(ctx, modes[s], io, s < 3 || tail, nullptr, st));
     }
     return MX_OK;
   }

@@ -10,120 +10,9 @@
 #include "kernels.cuh"
 #include "local.cuh"
 #include "regfft.cuh"
+#include "xrows.cuh"
 
 namespace mx {
-
-// Threads of the x kernels' FFT phase: the 3R lines of S threads, rounded up
-// to whole warps (the extra threads transform scratch lines).  The load and
-// store phases use all NT >= that many threads, so that a block with few
-// rows still has many memory requests in flight.
-template <int S, int R> struct XfShape {
-  static constexpr int NF = (3 * R * S + 31) / 32 * 32;
-  static constexpr int lines = NF / S;  // shared-memory lines, scratch included
-};
-
-// The 3R line transforms of M = E*S points of an x kernel's block, in place
-// in shared memory (line l at l * P), ending with a block barrier.  Where
-// every thread can take whole radix-8 butterflies (3RM / NT >= 8 elements
-// each) all NT threads run the Stockham passes of block_fft (short chains per
-// thread, a barrier per pass); otherwise the NF threads of the lines run the
-// two-step register transform (twM[q] = W_M^q either way).
-template <int E, int S, int R, int NT, bool INV>
-__device__ __forceinline__ void x_line_ffts(float2* sm, const float2* __restrict__ twM) {
-  constexpr int M = E * S;
-  constexpr int P = LineFft<E, S>::kPitch;
-  constexpr int EPT = 3 * R * M / NT;
-  if constexpr ((3 * R * M) % NT == 0 && EPT >= 8) {
-    block_fft<INV, float2, EPT, NT>(sm, M, 3 * R, lines1(P), 1, twM, 1);
-  } else {
-    if ((int)threadIdx.x < XfShape<S, R>::NF) line_fft<E, S, INV>(sm + (threadIdx.x / S) * P, threadIdx.x % S, twM);
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// x forward (r2c), R rows per block, 3R lines of M = E*S points.
-// ---------------------------------------------------------------------------
-// Rows row0 .. row0 + R - 1 of Ms m (the real row packed as z[n] = x[2n] +
-// i x[2n+1]) through the line FFT and the split step into w1.  COHERENT reads
-// m with plain loads (m written earlier in the same kernel), else through the
-// read-only path.
-template <int E, int S, int R, int NT, bool COHERENT>
-__device__ __forceinline__ void xf_rows(float2* sm, const float4* __restrict__ m, const Grid& g, float ms,
-                                        const float* __restrict__ ms_map, float2* __restrict__ w1, int row0,
-                                        const float2* __restrict__ twM, const float2* __restrict__ twP) {
-  constexpr int M = E * S;
-  constexpr int P = LineFft<E, S>::kPitch;
-  constexpr int NF = XfShape<S, R>::NF;
-  static_assert(NT >= NF && NT % 32 == 0, "xf thread count");
-  const int nrows = g.ny * g.nz;
-  const int tid = threadIdx.x;
-  // batches of kB cell pairs per thread: 2 kB independent loads in flight
-  constexpr int kB = (R * M + NT - 1) / NT < 4 ? (R * M + NT - 1) / NT : 4;
-  for (int e0 = tid; e0 < R * M; e0 += NT * kB) {
-    float4 a[kB], b[kB];
-    float sa[kB], sb[kB];
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = e0 + u * NT;
-      const int r = e / M, n = e % M;
-      const int row = row0 + r;
-      a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      sa[u] = sb[u] = ms;
-      if (e < R * M && row < nrows) {
-        const long cell = (long)row * g.nx;
-        const int i0 = 2 * n, i1 = i0 + 1;
-        if (i0 < g.nx) {
-          a[u] = COHERENT ? m[cell + i0] : __ldg(&m[cell + i0]);
-          if (ms_map) sa[u] = __ldg(&ms_map[cell + i0]);
-        }
-        if (i1 < g.nx) {
-          b[u] = COHERENT ? m[cell + i1] : __ldg(&m[cell + i1]);
-          if (ms_map) sb[u] = __ldg(&ms_map[cell + i1]);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = e0 + u * NT;
-      if (e >= R * M) break;
-      const int r = e / M, n = e % M;
-      // zero outside the grid (a, b are zero there)
-      sm[(3 * r + 0) * P + n] = make_float2(sa[u] * a[u].x, sb[u] * b[u].x);
-      sm[(3 * r + 1) * P + n] = make_float2(sa[u] * a[u].y, sb[u] * b[u].y);
-      sm[(3 * r + 2) * P + n] = make_float2(sa[u] * a[u].z, sb[u] * b[u].z);
-    }
-  }
-  __syncthreads();
-  x_line_ffts<E, S, R, NT, false>(sm, twM);
-  const long cs = (long)g.nz * g.ny * g.Hx;
-  // batches of kB outputs per thread: the twiddle loads of a batch go out together
-  constexpr int kBo = (3 * R * (M + 1) + NT - 1) / NT <= 9 ? (3 * R * (M + 1) + NT - 1) / NT : 4;
-  for (int e0 = tid; e0 < 3 * R * (M + 1); e0 += NT * kBo) {
-    float2 tw[kBo];
-#pragma unroll
-    for (int u = 0; u < kBo; ++u) {
-      const int e = e0 + u * NT;
-      tw[u] = e < 3 * R * (M + 1) ? __ldg(&twP[e % (M + 1)]) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < kBo; ++u) {
-      const int e = e0 + u * NT;
-      if (e >= 3 * R * (M + 1)) break;
-      const int line = e / (M + 1), k = e % (M + 1);
-      const int r = line / 3, c = line % 3;
-      const int row = row0 + r;
-      if (row >= nrows) continue;
-      const float2* L = sm + line * P;
-      const float2 zk = L[k == M ? 0 : k];
-      const float2 zc = cconj(L[k == 0 ? 0 : M - k]);
-      const float2 Ev = cscale(cadd(zk, zc), 0.5f);
-      const float2 D = csub(zk, zc);
-      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-      w1[c * cs + (long)row * g.Hx + k] = cadd(Ev, cmul(tw[u], O));
-    }
-  }
-}
 
 template <int E, int S, int R, int NT>
 __global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Grid g, float ms,
@@ -137,59 +26,6 @@ __global__ void __launch_bounds__(NT) xf_kernel(const float4* __restrict__ m, Gr
 // ---------------------------------------------------------------------------
 // x inverse (c2r).
 // ---------------------------------------------------------------------------
-// The c2r transforms of rows row0 .. row0 + R - 1 into shared memory:
-// afterwards element n of line 3 r + c holds H_c of cells 2n (real part) and
-// 2n + 1 (imaginary part) of row row0 + r.
-template <int E, int S, int R, int NT>
-__device__ __forceinline__ void xi_rows(float2* sm, const float2* __restrict__ w1, const Grid& g, int row0,
-                                        const float2* __restrict__ twM, const float2* __restrict__ twP) {
-  constexpr int M = E * S;
-  constexpr int P = LineFft<E, S>::kPitch;
-  constexpr int NF = XfShape<S, R>::NF;
-  static_assert(NT >= NF && NT % 32 == 0, "xi thread count");
-  const int nrows = g.ny * g.nz;
-  const int tid = threadIdx.x;
-  const long cs = (long)g.nz * g.ny * g.Hx;
-  // batches of kB elements per thread: 2 kB independent loads in flight
-  constexpr int kB = (3 * R * M + NT - 1) / NT <= 8 ? (3 * R * M + NT - 1) / NT : 4;
-  for (int e0 = tid; e0 < 3 * R * M; e0 += NT * kB) {
-    float2 A[kB], Bv[kB];
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = e0 + u * NT;
-      const int line = e / M, k = e % M;
-      const int r = line / 3, c = line % 3;
-      A[u] = Bv[u] = make_float2(0.f, 0.f);
-      if (e < 3 * R * M && row0 + r < nrows) {
-        const float2* X = w1 + c * cs + (long)(row0 + r) * g.Hx;
-        A[u] = __ldg(&X[k]);
-        Bv[u] = __ldg(&X[M - k]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      const int e = e0 + u * NT;
-      if (e >= 3 * R * M) break;
-      const int k = e % M;
-      const float2 a = A[u], b = cconj(Bv[u]);
-      const float2 Sv = cadd(a, b);
-      const float2 t = cmul(cconj(__ldg(&twP[k])), csub(a, b));
-      sm[(e / M) * P + k] = make_float2(Sv.x - t.y, Sv.y + t.x);
-    }
-  }
-  __syncthreads();
-  x_line_ffts<E, S, R, NT, true>(sm, twM);
-}
-
-// H_demag of cell i of row r from the c2r lines
-template <int E, int S>
-__device__ __forceinline__ float3 xi_cell(const float2* sm, int r, int i) {
-  constexpr int P = LineFft<E, S>::kPitch;
-  const float2* L = sm + (3 * r) * P + (i >> 1);
-  const float2 hx = L[0], hy = L[P], hz = L[2 * P];
-  return (i & 1) ? make_float3(hx.y, hy.y, hz.y) : make_float3(hx.x, hy.x, hz.x);
-}
-
 template <int E, int S, int R, int NT>
 __global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, Grid g, float4* __restrict__ hd,
                                                 const float2* __restrict__ twM, const float2* __restrict__ twP) {
@@ -217,7 +53,7 @@ __global__ void __launch_bounds__(NT) xi_kernel(const float2* __restrict__ w1, G
 // ---------------------------------------------------------------------------
 template <int MODE, bool DMI, int E, int S, int R, int NT>
 __device__ __forceinline__ void xr_cells(const float2* sm, const StageIO& io, const Grid& g, const LocalCoef& c,
-                                         int row0, int* flag) {
+                                         int row0, float4* __restrict__ hd_out, int* flag) {
   // KC cells per thread and round with every cell's own loads issued first
   constexpr int KC = (R * E * S + NT - 1) / NT < 3 ? (R * E * S + NT - 1) / NT : 3;
   const int nrows = g.ny * g.nz;
@@ -238,7 +74,9 @@ __device__ __forceinline__ void xr_cells(const float2* sm, const StageIO& io, co
       const int r = e / g.nx, i = e - r * g.nx;
       const int row = row0 + r;
       const int z = row / g.ny, y = row - z * g.ny;
-      local_cell_in<MODE, DMI>(io, g, c, i, y, z, idx[u], xi_cell<E, S>(sm, r, i), v[u], flag);
+      const float3 h = xi_cell<E, S>(sm, r, i);
+      if (hd_out) hd_out[idx[u]] = make_float4(h.x, h.y, h.z, 0.f);
+      local_cell_in<MODE, DMI>(io, g, c, i, y, z, idx[u], h, v[u], flag);
     }
   }
 }
@@ -247,16 +85,16 @@ template <int E, int S, int R, int NT, bool DMI>
 __global__ void __launch_bounds__(NT) xr_kernel(float2* __restrict__ w1, Grid g, float ms,
                                                 const float* __restrict__ ms_map, const float2* __restrict__ twM,
                                                 const float2* __restrict__ twP, StageIO io, LocalCoef c, int mode,
-                                                int xf_next, int* flag) {
+                                                int xf_next, float4* __restrict__ hd_out, int* flag) {
   extern __shared__ float2 sm[];
   const int row0 = blockIdx.x * R;
   pdl_wait();
   xi_rows<E, S, R, NT>(sm, w1, g, row0, twM, twP);
   switch (mode) {
-    case LM_RK4_S0: xr_cells<LM_RK4_S0, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
-    case LM_RK4_S1: xr_cells<LM_RK4_S1, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
-    case LM_RK4_S2: xr_cells<LM_RK4_S2, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
-    default: xr_cells<LM_RK4_S3, DMI, E, S, R, NT>(sm, io, g, c, row0, flag); break;
+    case LM_RK4_S0: xr_cells<LM_RK4_S0, DMI, E, S, R, NT>(sm, io, g, c, row0, hd_out, flag); break;
+    case LM_RK4_S1: xr_cells<LM_RK4_S1, DMI, E, S, R, NT>(sm, io, g, c, row0, hd_out, flag); break;
+    case LM_RK4_S2: xr_cells<LM_RK4_S2, DMI, E, S, R, NT>(sm, io, g, c, row0, hd_out, flag); break;
+    default: xr_cells<LM_RK4_S3, DMI, E, S, R, NT>(sm, io, g, c, row0, hd_out, flag); break;
   }
   if (!xf_next) return;
   __syncthreads();  // the block's io.out rows are written; the c2r lines are read
@@ -426,7 +264,8 @@ static mx_status run_xi(mx_ctx* ctx, float4* hd, cudaStream_t st, bool setup) {
 }
 
 template <int E, int S, int R, int NT>
-static mx_status run_xr(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st, bool setup) {
+static mx_status run_xr(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st,
+                        bool setup) {
   const size_t sm = x_smem<E, S, R>();
   if (setup) {
     MX_CUDA_TRY(cudaFuncSetAttribute(xr_kernel<E, S, R, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -441,10 +280,10 @@ static mx_status run_xr(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, 
   const dim3 grid((nrows + R - 1) / R);
   if (c.dmi)
     launch_pdl(xr_kernel<E, S, R, NT, true>, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map,
-               ctx->tw_m, ctx->tw_x, io, c, mode, xf_next ? 1 : 0, ctx->flag);
+               ctx->tw_m, ctx->tw_x, io, c, mode, xf_next ? 1 : 0, hd_out, ctx->flag);
   else
     launch_pdl(xr_kernel<E, S, R, NT, false>, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map,
-               ctx->tw_m, ctx->tw_x, io, c, mode, xf_next ? 1 : 0, ctx->flag);
+               ctx->tw_m, ctx->tw_x, io, c, mode, xf_next ? 1 : 0, hd_out, ctx->flag);
   return launch_check("xr_kernel");
 }
 
@@ -454,7 +293,6 @@ static mx_status run_xr(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, 
 // second (set-up prepares both).  The few-rows variant runs kFewRowsNT
 // threads, most of which only load and store.
 static constexpr int kMinBlocks = 2 * 152;
-static constexpr int kFewRowsNT = 192;
 
 template <int E, int S, int RB, int RS>
 static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
@@ -477,22 +315,24 @@ static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool invers
 // have fewer blocks than two per SM, where the step is bound by its kernel
 // boundaries); MX_ERR_UNSUPPORTED for the others.
 template <int E, int S, int RB, int RS>
-static mx_status xr_pass_rs(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st, bool setup) {
+static mx_status xr_pass_rs(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st,
+                            bool setup) {
   constexpr int NS = XfShape<S, RS>::NF > kFewRowsNT ? XfShape<S, RS>::NF : kFewRowsNT;
   const int nrows = ctx->g.ny * ctx->g.nz;
   if ((nrows + RB - 1) / RB >= kMinBlocks) return MX_ERR_UNSUPPORTED;
-  return run_xr<E, S, RS, NS>(ctx, mode, io, xf_next, st, setup);
+  return run_xr<E, S, RS, NS>(ctx, mode, io, xf_next, hd_out, st, setup);
 }
 
-static mx_status xr_pass(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st, bool setup) {
+static mx_status xr_pass(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st,
+                         bool setup) {
   switch (ctx->g.Px / 2) {
-    case 1024: return xr_pass_rs<32, 32, 2, 1>(ctx, mode, io, xf_next, st, setup);
-    case 512: return xr_pass_rs<32, 16, 4, 1>(ctx, mode, io, xf_next, st, setup);
-    case 256: return xr_pass_rs<16, 16, 4, 1>(ctx, mode, io, xf_next, st, setup);
-    case 128: return xr_pass_rs<16, 8, 8, 2>(ctx, mode, io, xf_next, st, setup);
-    case 64: return xr_pass_rs<8, 8, 8, 2>(ctx, mode, io, xf_next, st, setup);
-    case 32: return xr_pass_rs<32, 1, 32, 4>(ctx, mode, io, xf_next, st, setup);
-    case 16: return xr_pass_rs<16, 1, 32, 4>(ctx, mode, io, xf_next, st, setup);
+    case 1024: return xr_pass_rs<32, 32, 2, 1>(ctx, mode, io, xf_next, hd_out, st, setup);
+    case 512: return xr_pass_rs<32, 16, 4, 1>(ctx, mode, io, xf_next, hd_out, st, setup);
+    case 256: return xr_pass_rs<16, 16, 4, 1>(ctx, mode, io, xf_next, hd_out, st, setup);
+    case 128: return xr_pass_rs<16, 8, 8, 2>(ctx, mode, io, xf_next, hd_out, st, setup);
+    case 64: return xr_pass_rs<8, 8, 8, 2>(ctx, mode, io, xf_next, hd_out, st, setup);
+    case 32: return xr_pass_rs<32, 1, 32, 4>(ctx, mode, io, xf_next, hd_out, st, setup);
+    case 16: return xr_pass_rs<16, 1, 32, 4>(ctx, mode, io, xf_next, hd_out, st, setup);
     default: return MX_ERR_UNSUPPORTED;
   }
 }
@@ -517,17 +357,17 @@ mx_status fast_setup(mx_ctx* ctx) {
                 x_pass(ctx, nullptr, nullptr, true, nullptr, true) == MX_OK;
   ctx->yz2d = ctx->fused_yz && ctx->g.Pz == 1 && yz2d_dispatch(ctx, nullptr, true) == MX_OK;
   StageIO none{};
-  ctx->xrow = ctx->fast_x && xr_pass(ctx, LM_RK4_S0, none, false, nullptr, true) == MX_OK;
+  ctx->xrow = ctx->fast_x && xr_pass(ctx, LM_RK4_S0, none, false, nullptr, nullptr, true) == MX_OK;
   clear_error();
   return MX_OK;
 }
 
-mx_status fast_row_stage(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st) {
+mx_status fast_row_stage(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st) {
   if (mode < LM_RK4_S0 || mode > LM_RK4_S3) {
     set_error("fast_row_stage: bad mode");
     return MX_ERR_INVALID_ARG;
   }
-  return xr_pass(ctx, mode, io, xf_next, st, false);
+  return xr_pass(ctx, mode, io, xf_next, hd_out, st, false);
 }
 
 mx_status fast_x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st) {

@@ -55,9 +55,12 @@ mx_status plane_stage_xlocal(mx_ctx* ctx, int mode, const StageIO& io, cudaStrea
 // The y/z passes of demag_field alone (w1 in place, after the forward x pass).
 mx_status demag_yz(mx_ctx* ctx, cudaStream_t st);
 // One RK4 stage's row kernel on grids with ctx->xrow (demag_fast.cu): the
-// inverse x pass of w1, the local stage of `mode`, and with xf_next the
-// forward x pass of io.out into w1 for the next stage.
-mx_status fast_row_stage(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, cudaStream_t st);
+// inverse x pass of w1, the local stage of `mode` (with hd_out, the demag
+// field of io.m is also written there), and with xf_next the forward x pass
+// of io.out into w1 for the next stage.
+mx_status fast_row_stage(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st);
+// Whether RK4 steps of this context run as y/z passes plus row kernels (api.cu).
+bool row_steps(const mx_ctx* ctx, int method);
 mx_status plane_spectrum_out(mx_ctx* ctx, float* out, cudaStream_t st);
 
 // demag_quad.cu: the four-CTA y/z plane kernel (setup: check the grid fits and
