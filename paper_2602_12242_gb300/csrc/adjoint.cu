@@ -239,6 +239,20 @@ struct AdjRowArgs {
   float4* gm_out;
 };
 
+// begin of a reverse step at one cell (lam_u4 = J_N(u4)^T lam_acc with u4's
+// norm in mnew.w, lam_acc = lam_u4) and the prep of its last stage
+template <bool DMI>
+__device__ __forceinline__ void adj_begin_cell(const AdjRowArgs& a, const float4* __restrict__ mnew, const Grid& g,
+                                               const LocalCoef& c, float dt, int i, int y, int z, long idx) {
+  const float4 n4 = mnew[idx];
+  const float3 nc = f3(n4);
+  const float3 l = f3(a.lam_acc[idx]);
+  const float3 lu = (1.f / n4.w) * (l - dot3(nc, l) * nc);
+  a.lam_u4[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+  a.lam_acc[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
+  prep_cell<DMI>(a.m_prev, a.hd_prev, g, c, i, y, z, idx, (dt / 6.f) * lu, a.wbuf_out, a.gm_out);
+}
+
 template <bool DMI, int R, int NT>
 __device__ __forceinline__ void adj_row_begin_cells(const AdjRowArgs& a, const Grid& g, const LocalCoef& c, float dt,
                                                     int row0) {
@@ -247,18 +261,14 @@ __device__ __forceinline__ void adj_row_begin_cells(const AdjRowArgs& a, const G
     const int r = e / g.nx, i = e - r * g.nx;
     const int row = row0 + r;
     const int z = row / g.ny, y = row - z * g.ny;
-    const long idx = (long)row * g.nx + i;
-    const float4 n4 = a.mnew[idx];
-    const float3 nc = f3(n4);
-    const float3 l = f3(a.lam_acc[idx]);
-    const float3 lu = (1.f / n4.w) * (l - dot3(nc, l) * nc);
-    a.lam_u4[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
-    a.lam_acc[idx] = make_float4(lu.x, lu.y, lu.z, 0.f);
-    prep_cell<DMI>(a.m_prev, a.hd_prev, g, c, i, y, z, idx, (dt / 6.f) * lu, a.wbuf_out, a.gm_out);
+    adj_begin_cell<DMI>(a, a.mnew, g, c, dt, i, y, z, (long)row * g.nx + i);
   }
 }
 
-template <bool DMI, int STAGE, int E, int S, int R, int NT>
+// STAGE 0 with CHAIN: after the finish, the begin of the step before at the
+// same cell (its result is this step's start state a.m) with the prep of its
+// last stage (a.m_prev, a.hd_prev -> a.wbuf_out, a.gm_out).
+template <bool DMI, int STAGE, int E, int S, int R, int NT, bool CHAIN = false>
 __device__ __forceinline__ void adj_row_cells(const float2* sm, const AdjRowArgs& a, const Grid& g,
                                               const LocalCoef& c, float dt, int row0) {
   const int total = min(R, g.ny * g.nz - row0) * g.nx;
@@ -270,6 +280,7 @@ __device__ __forceinline__ void adj_row_cells(const float2* sm, const AdjRowArgs
     const float3 nk = finish_cell_v<DMI, STAGE>(a.m, a.wbuf, xi_cell<E, S>(sm, r, i), a.gm, a.lam_u4, a.lam_acc,
                                                 a.dms, g, c, dt, i, y, z, idx);
     if (STAGE > 0) prep_cell<DMI>(a.m_prev, a.hd_prev, g, c, i, y, z, idx, nk, a.wbuf_out, a.gm_out);
+    if (STAGE == 0 && CHAIN) adj_begin_cell<DMI>(a, a.m, g, c, dt, i, y, z, idx);
   }
 }
 
@@ -291,7 +302,7 @@ template <int E, int S, int R, int NT, bool DMI>
 __global__ void __launch_bounds__(NT) adj_row_kernel(float2* __restrict__ w1, Grid g, float ms,
                                                      const float* __restrict__ ms_map, const float2* __restrict__ twM,
                                                      const float2* __restrict__ twP, AdjRowArgs a, LocalCoef c,
-                                                     float dt, int stage) {
+                                                     float dt, int stage, int chain) {
   extern __shared__ float2 sm[];
   const int row0 = blockIdx.x * R;
   pdl_wait();
@@ -300,7 +311,13 @@ __global__ void __launch_bounds__(NT) adj_row_kernel(float2* __restrict__ w1, Gr
     case 3: adj_row_cells<DMI, 3, E, S, R, NT>(sm, a, g, c, dt, row0); break;
     case 2: adj_row_cells<DMI, 2, E, S, R, NT>(sm, a, g, c, dt, row0); break;
     case 1: adj_row_cells<DMI, 1, E, S, R, NT>(sm, a, g, c, dt, row0); break;
-    default: adj_row_cells<DMI, 0, E, S, R, NT>(sm, a, g, c, dt, row0); return;
+    default:
+      if (!chain) {
+        adj_row_cells<DMI, 0, E, S, R, NT>(sm, a, g, c, dt, row0);
+        return;
+      }
+      adj_row_cells<DMI, 0, E, S, R, NT, true>(sm, a, g, c, dt, row0);
+      break;
   }
   __syncthreads();  // the block's rows of the new w are written; the c2r lines are read
   xf_rows<E, S, R, NT, true>(sm, a.wbuf_out, g, ms, ms_map, w1, row0, twM, twP);
@@ -314,6 +331,7 @@ struct AdjRowLaunch {
   float dt;
   int stage;
   bool begin;
+  bool chain;
   cudaStream_t st;
   template <int E, int S, int R, int NT> mx_status run() {
     const size_t sm = sizeof(float2) * XfShape<S, R>::lines * LineFft<E, S>::kPitch;
@@ -330,7 +348,7 @@ struct AdjRowLaunch {
     }
     auto k = c.dmi ? adj_row_kernel<E, S, R, NT, true> : adj_row_kernel<E, S, R, NT, false>;
     launch_pdl(k, grid, dim3(NT), sm, st, ctx->w1, g, (float)ctx->p.Ms, ctx->ms_map, ctx->tw_m, ctx->tw_x, *a, c,
-               dt, stage);
+               dt, stage, chain ? 1 : 0);
     return launch_check("adj_row_kernel");
   }
 };
@@ -519,7 +537,8 @@ mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, do
   const bool demag = ctx->p.demag != 0;
   if (use_graph && !w->g_fwd && w->nsteps >= w->every) {
     MX_TRY(capture_graph(ctx, &w->g_fwd, [&](cudaStream_t cs) -> mx_status {
-      for (int s = 0; s < w->every; ++s) MX_TRY(rk4_step_direct(ctx, cur, dt, cs));
+      // consecutive steps on cur: each leaves the next one's forward x pass
+      for (int s = 0; s < w->every; ++s) MX_TRY(rk4_step_direct(ctx, cur, dt, cs, s == 0, true));
       return MX_OK;
     }));
   }
@@ -546,7 +565,7 @@ mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, do
     } else if (use_graph && len == w->every && w->g_fwd) {
       MX_CUDA_TRY(cudaGraphLaunch(w->g_fwd, st));
     } else {
-      for (int s = 0; s < len; ++s) MX_TRY(rk4_step_direct(ctx, cur, dt, st));
+      for (int s = 0; s < len; ++s) MX_TRY(rk4_step_direct(ctx, cur, dt, st, s == 0, true));
     }
   }
   w->last_stored = w->segst != nullptr;
@@ -556,8 +575,12 @@ mx_status adjoint_forward(mx_ctx* ctx, const float4* m0_raw, float4* m_final, do
   return MX_OK;
 }
 
+// With row kernels, `first` runs the begin of step i on its own and `chain`
+// (i > 0 within a stored segment) folds the begin of step i - 1 into the
+// last kernel of step i, so the next call is made with first = false.
 template <bool DMI>
-static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, cudaStream_t st) {
+static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, cudaStream_t st,
+                                       bool first, bool chain) {
   const Grid& g = ctx->g;
   const long nc = g.ncell;
   const LocalCoef c = local_coef(ctx);
@@ -577,8 +600,10 @@ static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt,
     // row kernels: begin + prep of stage 3, then per stage the y/z passes of
     // w's spectrum and the finish (+ prep of the stage before) row kernel
     AdjRowArgs a{mnew, nullptr, nullptr, nullptr, w->lam_u4, w->lam_acc, w->dms, states[3], hd[3], wb[0], gmb[0]};
-    AdjRowLaunch L{ctx, &a, dt, 0, true, st};
-    MX_TRY(few_rows_dispatch(g.Px / 2, L));
+    if (first) {
+      AdjRowLaunch L{ctx, &a, dt, 0, true, false, st};
+      MX_TRY(few_rows_dispatch(g.Px / 2, L));
+    }
     int b = 0;
     for (int q = 3; q >= 0; --q) {
       MX_TRY(demag_yz(ctx, st));
@@ -589,7 +614,16 @@ static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt,
       a.hd_prev = q > 0 ? hd[q - 1] : nullptr;
       a.wbuf_out = wb[b ^ 1];
       a.gm_out = gmb[b ^ 1];
-      AdjRowLaunch Lq{ctx, &a, dt, q, false, st};
+      if (q == 0 && chain) {
+        // the begin of step i - 1: its last stage state and demag field, and
+        // its w and g_m into the first buffer pair
+        const float4* Sp = w->segst + (long)(i - 1) * 3 * nc;
+        a.m_prev = Sp + 2 * nc;
+        a.hd_prev = demag ? w->seghd + (long)(i - 1) * 4 * nc + 3 * nc : w->hd4;
+        a.wbuf_out = wb[0];
+        a.gm_out = gmb[0];
+      }
+      AdjRowLaunch Lq{ctx, &a, dt, q, false, q == 0 && chain, st};
       MX_TRY(few_rows_dispatch(g.Px / 2, Lq));
       b ^= 1;
     }
@@ -628,10 +662,11 @@ static mx_status stored_reverse_step_t(mx_ctx* ctx, AdjWork* w, int i, float dt,
   return MX_OK;
 }
 
-static mx_status stored_reverse_step(mx_ctx* ctx, AdjWork* w, int i, float dt, bool demag, bool dmi,
+static mx_status stored_reverse_step(mx_ctx* ctx, AdjWork* w, int i, int len, float dt, bool demag, bool dmi,
                                      cudaStream_t st) {
-  return dmi ? stored_reverse_step_t<true>(ctx, w, i, dt, demag, st)
-             : stored_reverse_step_t<false>(ctx, w, i, dt, demag, st);
+  const bool first = i == len - 1, chain = i > 0;
+  return dmi ? stored_reverse_step_t<true>(ctx, w, i, dt, demag, st, first, chain)
+             : stored_reverse_step_t<false>(ctx, w, i, dt, demag, st, first, chain);
 }
 
 template <int STAGE>
@@ -676,7 +711,7 @@ mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0
         }));
       if (!w->g_rev)
         MX_TRY(capture_graph(ctx, &w->g_rev, [&](cudaStream_t cs) -> mx_status {
-          for (int i = w->every - 1; i >= 0; --i) MX_TRY(stored_reverse_step(ctx, w, i, dt, demag, dmi, cs));
+          for (int i = w->every - 1; i >= 0; --i) MX_TRY(stored_reverse_step(ctx, w, i, w->every, dt, demag, dmi, cs));
           return MX_OK;
         }));
     }
@@ -695,7 +730,7 @@ mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0
       if (use_graph && len == w->every && w->g_rev)
         MX_CUDA_TRY(cudaGraphLaunch(w->g_rev, st));
       else
-        for (int i = len - 1; i >= 0; --i) MX_TRY(stored_reverse_step(ctx, w, i, dt, demag, dmi, st));
+        for (int i = len - 1; i >= 0; --i) MX_TRY(stored_reverse_step(ctx, w, i, len, dt, demag, dmi, st));
     }
     w->last_stored = false;  // the segment buffers now hold the first segment
     adj_end_kernel<<<nb, 256, 0, st>>>(w->raw, w->lam_acc, grad_m0, w->dms, grad_ms, nc);

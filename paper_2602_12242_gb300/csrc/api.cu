@@ -166,8 +166,8 @@ static mx_status enqueue_step(mx_ctx* ctx, float4* m, double dt, int method, cud
   return MX_OK;
 }
 
-mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st) {
-  return enqueue_step(ctx, m, dt, MX_RK4, st);
+mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st, bool lead, bool tail) {
+  return enqueue_step(ctx, m, dt, MX_RK4, st, lead, tail);
 }
 
 // sums of |a - b|^2 and |b|^2 over the xyz of float4 records

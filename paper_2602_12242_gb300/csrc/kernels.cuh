@@ -95,7 +95,9 @@ mx_status adjoint_backward(mx_ctx* ctx, const float4* lam_final, float4* grad_m0
 bool adjoint_recorded(const mx_ctx* ctx);
 
 // api.cu
-mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st);
+// With row kernels (row_steps), `lead` runs the forward x pass of m first
+// (else w1 must hold it) and `tail` leaves that of the new m in w1.
+mx_status rk4_step_direct(mx_ctx* ctx, float4* m, double dt, cudaStream_t st, bool lead = true, bool tail = false);
 
 // local.cu
 enum LocalMode { LM_HEFF = 0, LM_RHS, LM_RK4_S0, LM_RK4_S1, LM_RK4_S2, LM_RK4_S3, LM_EULER };
