@@ -292,7 +292,6 @@ static mx_status run_xr(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, 
 // row count would give fewer than two blocks per SM with the first take the
 // second (set-up prepares both).  The few-rows variant runs kFewRowsNT
 // threads, most of which only load and store.
-static constexpr int kMinBlocks = 2 * 152;
 
 template <int E, int S, int RB, int RS>
 static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
@@ -305,36 +304,32 @@ static mx_status x_pass_rs(mx_ctx* ctx, const float4* m, float4* hd, bool invers
     if (s == MX_OK) s = run_xf<E, S, RS, NS>(ctx, m, st, true);
     return s;
   }
-  const int nrows = ctx->g.ny * ctx->g.nz;
-  if ((nrows + RB - 1) / RB >= kMinBlocks)
+  if (!few_rows(ctx->g))
     return inverse ? run_xi<E, S, RB, NB>(ctx, hd, st, false) : run_xf<E, S, RB, NB>(ctx, m, st, false);
   return inverse ? run_xi<E, S, RS, NS>(ctx, hd, st, false) : run_xf<E, S, RS, NS>(ctx, m, st, false);
 }
 
-// The row kernel exists for the few-rows variant only (grids whose x passes
+// The row kernel exists for the few-row blocks only (grids whose x passes
 // have fewer blocks than two per SM, where the step is bound by its kernel
 // boundaries); MX_ERR_UNSUPPORTED for the others.
-template <int E, int S, int RB, int RS>
-static mx_status xr_pass_rs(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st,
-                            bool setup) {
-  constexpr int NS = XfShape<S, RS>::NF > kFewRowsNT ? XfShape<S, RS>::NF : kFewRowsNT;
-  const int nrows = ctx->g.ny * ctx->g.nz;
-  if ((nrows + RB - 1) / RB >= kMinBlocks) return MX_ERR_UNSUPPORTED;
-  return run_xr<E, S, RS, NS>(ctx, mode, io, xf_next, hd_out, st, setup);
-}
+struct XrLaunch {
+  mx_ctx* ctx;
+  int mode;
+  const StageIO* io;
+  bool xf_next;
+  float4* hd_out;
+  cudaStream_t st;
+  bool setup;
+  template <int E, int S, int R, int NT> mx_status run() {
+    return run_xr<E, S, R, NT>(ctx, mode, *io, xf_next, hd_out, st, setup);
+  }
+};
 
 static mx_status xr_pass(mx_ctx* ctx, int mode, const StageIO& io, bool xf_next, float4* hd_out, cudaStream_t st,
                          bool setup) {
-  switch (ctx->g.Px / 2) {
-    case 1024: return xr_pass_rs<32, 32, 2, 1>(ctx, mode, io, xf_next, hd_out, st, setup);
-    case 512: return xr_pass_rs<32, 16, 4, 1>(ctx, mode, io, xf_next, hd_out, st, setup);
-    case 256: return xr_pass_rs<16, 16, 4, 1>(ctx, mode, io, xf_next, hd_out, st, setup);
-    case 128: return xr_pass_rs<16, 8, 8, 2>(ctx, mode, io, xf_next, hd_out, st, setup);
-    case 64: return xr_pass_rs<8, 8, 8, 2>(ctx, mode, io, xf_next, hd_out, st, setup);
-    case 32: return xr_pass_rs<32, 1, 32, 4>(ctx, mode, io, xf_next, hd_out, st, setup);
-    case 16: return xr_pass_rs<16, 1, 32, 4>(ctx, mode, io, xf_next, hd_out, st, setup);
-    default: return MX_ERR_UNSUPPORTED;
-  }
+  if (!few_rows(ctx->g)) return MX_ERR_UNSUPPORTED;
+  XrLaunch L{ctx, mode, &io, xf_next, hd_out, st, setup};
+  return few_rows_dispatch(ctx->g.Px / 2, L);
 }
 
 static mx_status x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, cudaStream_t st, bool setup) {
@@ -342,7 +337,7 @@ static mx_status x_pass(mx_ctx* ctx, const float4* m, float4* hd, bool inverse, 
     case 1024: return x_pass_rs<32, 32, 2, 1>(ctx, m, hd, inverse, st, setup);
     case 512: return x_pass_rs<32, 16, 4, 1>(ctx, m, hd, inverse, st, setup);
     case 256: return x_pass_rs<16, 16, 4, 1>(ctx, m, hd, inverse, st, setup);
-    case 128: return x_pass_rs<16, 8, 8, 2>(ctx, m, hd, inverse, st, setup);
+    case 128: return x_pass_rs<16, 8, 8, 1>(ctx, m, hd, inverse, st, setup);
     case 64: return x_pass_rs<8, 8, 8, 2>(ctx, m, hd, inverse, st, setup);
     case 32: return x_pass_rs<32, 1, 32, 4>(ctx, m, hd, inverse, st, setup);
     case 16: return x_pass_rs<16, 1, 32, 4>(ctx, m, hd, inverse, st, setup);

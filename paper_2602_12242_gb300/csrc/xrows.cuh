@@ -180,6 +180,24 @@ __device__ __forceinline__ float3 xi_cell(const float2* sm, int r, int i) {
   return (i & 1) ? make_float3(hx.y, hy.y, hz.y) : make_float3(hx.x, hy.x, hz.x);
 }
 
+// x blocks of a grid: many rows per block (many_rows(M) of them) unless that
+// gives fewer than kMinBlocks blocks; then the few-row blocks below.
+constexpr int kMinBlocks = 2 * 152;
+inline int many_rows(int half) {
+  switch (half) {
+    case 1024: return 2;
+    case 512:
+    case 256: return 4;
+    case 128:
+    case 64: return 8;
+    default: return 32;
+  }
+}
+inline bool few_rows(const Grid& g) {
+  const int rb = many_rows(g.Px / 2);
+  return (g.ny * g.nz + rb - 1) / rb < kMinBlocks;
+}
+
 // Threads of the few-row block with R rows of S-thread lines.
 template <int S, int R> constexpr int few_rows_nt() {
   return XfShape<S, R>::NF > kFewRowsNT ? XfShape<S, R>::NF : kFewRowsNT;
@@ -193,7 +211,7 @@ template <class F> mx_status few_rows_dispatch(int half, F& f) {
     case 1024: return f.template run<32, 32, 1, few_rows_nt<32, 1>()>();
     case 512: return f.template run<32, 16, 1, few_rows_nt<16, 1>()>();
     case 256: return f.template run<16, 16, 1, few_rows_nt<16, 1>()>();
-    case 128: return f.template run<16, 8, 2, few_rows_nt<8, 2>()>();
+    case 128: return f.template run<16, 8, 1, few_rows_nt<8, 1>()>();
     case 64: return f.template run<8, 8, 2, few_rows_nt<8, 2>()>();
     case 32: return f.template run<32, 1, 4, few_rows_nt<1, 4>()>();
     case 16: return f.template run<16, 1, 4, few_rows_nt<1, 4>()>();
