@@ -170,6 +170,8 @@ def algorithmic_bytes(cfg, P, ms_map=False, ku_map=False, axis_map=False):
         "x_inv": w1 + nc * 16,
         # RK4 stage average: (64 + 96 + 96 + 80) / 4 bytes per cell, plus the maps
         "local_stage": nc * (84 + maps),
+        # inverse x fused with the local stage: H_demag neither stored nor read
+        "x_inv_local": w1 + nc * (68 + maps),
         "normalize": nc * 32,
         "copy": nc * 32,
     }
@@ -178,7 +180,8 @@ def algorithmic_bytes(cfg, P, ms_map=False, ku_map=False, axis_map=False):
 CSRC = os.path.join(ROOT, "paper_2602_12242_gb300", "csrc")
 # translation unit that defines each kernel of the traffic table
 KERNEL_TU = {"yzq_kernel": "demag_quad.cu", "yzh_kernel": "demag_plane.cu", "xfk_kernel": "demag_plane.cu",
-             "xik_kernel": "demag_plane.cu", "xil_kernel": "demag_plane.cu", "local_kernel": "local.cu"}
+             "xik_kernel": "demag_plane.cu", "xil_kernel": "demag_plane.cu", "xr_kernel": "demag_fast.cu",
+             "local_kernel": "local.cu"}
 
 
 def kernel_sources(kernel):
@@ -292,6 +295,9 @@ def run_mx(args, rank, world, local, name, with_extras=True):
     res["launches_per_step"] = per_step
     res["gpu_launches"] = int(round(per_step * K)) + 1
     names = ctx.kernel_names()
+    if names.get("x_inv_local") == "xr_kernel":
+        # the row kernel also writes the next stage's spectrum (3 stages of 4)
+        ab["x_inv_local"] += 3 * (ab["x_inv"] - cfg["nx"] * cfg["ny"] * cfg["nz"] * 16) // 4
     dom = max(prof, key=lambda k: prof[k][0])
     tot = sum(v[0] for v in prof.values())
     kern = {k: {"kernel": names.get(k, k), "ms_total": round(v[0], 4), "launches": v[1],

@@ -302,7 +302,7 @@ def adjoint_report(nsteps=2000, every=100):
     g, gms = ctx.rk_backward(lam)
     e2.record()
     torch.cuda.synchronize()
-    return {"workload": "adjoint 128x128x1, 2000 RK4 steps, checkpoint every 100",
+    return {"workload": f"adjoint 128x128x1, {nsteps} RK4 steps, checkpoint every {every}",
             "plain_forward_ms": t_plain, "recorded_forward_ms": e0.elapsed_time(e1),
             "backward_ms": e1.elapsed_time(e2),
             "gradient_cost_over_plain_forward": e0.elapsed_time(e2) / t_plain,
@@ -406,8 +406,14 @@ def main():
     ap.add_argument("--insteps", type=int, default=5000)
     ap.add_argument("--judge", type=int, default=100)
     ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=2000)
+    ap.add_argument("--adj-every", type=int, default=100)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    if a.adjoint_only:
+        print(json.dumps(adjoint_report(a.adj_steps, a.adj_every)), flush=True)
+        return
     if a.mri:
         print(json.dumps(mri_report()), flush=True)
         return
