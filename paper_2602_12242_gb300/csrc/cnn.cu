@@ -277,103 +277,130 @@ __global__ void __launch_bounds__(kCnnThreads, 1) conv_tc_kernel(const bf16_t* _
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient of one layer: dW[tap][co][ci] += sum_cells dY[cell][co] *
-// x[cell + off(tap)][ci].  Block (chunk of 16 x 8 tiles, dz): the nine taps of
-// one dz share an (18 x 10) halo plane of x and the tile's dY, loaded once per
-// tile; each warp owns (tap, 16-row co tile, 8-column ci tile) output tiles of
-// M = COUT (16 per m tile), N = CIN, K = cells (one 16-cell row per k step).
-// dY is [cells][COUT] (COUT padded to 16), x [cells][CIN].
+// Weight gradient of one layer on the tcgen05 tensor cores:
+//   dW[tap][co][ci] += sum_cells dY[cell][co] * x[cell + off(tap)][ci].
+// Block (range of 16 x 8 output tiles, dz, ddy) owns the three taps
+// (dz, ddy, ddx = 0..2).  Per tile and tile row cy, three MMAs
+// D_ddx (co x ci) += dY^T (co x the 16 cells of row cy) X_ddx (those cells
+// shifted by the tap x ci), M = 128 (co, rows >= COUT zero), N = CIN, K = 16,
+// accumulated in tensor memory over all of the block's tiles.  Both operands
+// are MN-major (channels contiguous, one 16-byte row of 8 channels per cell,
+// core matrices adjacent along K 128 B apart, 8-channel groups SBO apart), so
+// they are 16-byte copies of the [cell][channel] activations: dY of the tile
+// (row q = cell cy * 16 + cx) and the tile's band of x rows for this ddy
+// (8 rows of 18 cells, row r * 18 + hx); the operand of (cy, ddx) starts at
+// row cy * 16 of dY and row cy * 18 + ddx of the band.
 // ---------------------------------------------------------------------------
+template <int CIN, int COUT> struct WgradShape {
+  static constexpr int HXp = kTX + 2;                    // band row: 18 cells
+  static constexpr int NROW = kTY * HXp;                 // 144 band cells
+  static constexpr uint32_t A_SBO = kTX * kTY * 16 + 16;  // 128 cells + 16 B pad (bank spread)
+  static constexpr uint32_t B_SBO = NROW * 16 + 16;
+  static constexpr uint32_t A_BYTES = 16 * A_SBO;
+  static constexpr uint32_t BUF = A_BYTES + (CIN / 8) * B_SBO;  // one tile's operands
+  static constexpr size_t smem = BUF;
+  static constexpr int TCOLS = 3 * CIN <= 64 ? 64 : (3 * CIN <= 128 ? 128 : 256);
+};
+
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kCnnThreads) wgrad_kernel(const bf16_t* __restrict__ x, const bf16_t* __restrict__ dy,
-                                                            float* __restrict__ dw, ConvDims d, int cin_real,
-                                                            int cout_real, int tiles_per_block) {
-  constexpr int XP = CIN + 8, YP = COUT + 8;
-  constexpr int MT = COUT / 16, NTL = CIN / 8;  // m tiles of 16, n tiles of 8
-  constexpr int TILES = 9 * MT * NTL;           // (tap in the dz plane, m tile, n tile)
-  constexpr int PER_WARP = (TILES + 7) / 8;
-  constexpr int HXp = kTX + 2, HYp = kTY + 2;   // halo plane
-  __shared__ __align__(16) bf16_t sx[HXp * HYp * XP];
-  __shared__ __align__(16) bf16_t sy[kTX * kTY * YP];
-  const int dz = blockIdx.y;
+__global__ void __launch_bounds__(kCnnThreads, 1) wgrad_tc_kernel(const bf16_t* __restrict__ x,
+                                                                  const bf16_t* __restrict__ dy,
+                                                                  float* __restrict__ dw, ConvDims d, int cin_real,
+                                                                  int cout_real, int tiles_per_block, int* flag) {
+  typedef WgradShape<CIN, COUT> W;
+  static_assert(COUT % 8 == 0 && COUT <= 128 && CIN % 16 == 0 && 3 * CIN <= 256, "wgrad shape");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
+  const int dz = blockIdx.y / 3, ddy = blockIdx.y % 3;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float acc[PER_WARP][4];
-#pragma unroll
-  for (int i = 0; i < PER_WARP; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  // dY^T (16 channel groups, those >= COUT/8 stay zero) then the x band
+  for (int i = tid; i < (int)(W::smem / 16); i += kCnnThreads) ((uint4*)smraw)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) tmem_alloc(&tbase, W::TCOLS);
+  if (tid == 0) mbar_init(&bar, 1);
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tb = tbase;
   const long plane = (long)d.nx * d.ny;
   const int t0 = blockIdx.x * tiles_per_block;
-  const int t1 = min(d.ntiles, t0 + tiles_per_block);
-  for (int t = t0; t < t1; ++t) {
+  const int n = max(0, min(d.ntiles, t0 + tiles_per_block) - t0);
+  constexpr uint32_t idesc = tc_idesc_bf16(128, CIN) | (1u << 15) | (1u << 16);  // A and B MN-major
+  // the copies of tile k, as one cp.async group
+  auto stage = [&](int k) {
+    unsigned char* sA = smraw;
+    unsigned char* sB = sA + W::A_BYTES;
     int b, z, y0, x0;
-    tile_coords(d, t, b, z, y0, x0);
+    tile_coords(d, t0 + k, b, z, y0, x0);
     const int gz = z + dz - 1;
-    // halo plane gz: cells (hy, hx) -> x cell (gz, y0 + hy - 1, x0 + hx - 1)
-    for (int e = tid; e < HXp * HYp * (CIN / 8); e += kCnnThreads) {
-      const int c = e / (CIN / 8), ch = e % (CIN / 8);
-      const int hx = c % HXp, hy = c / HXp;
-      const int gx = x0 + hx - 1, gy = y0 + hy - 1;
+    // band cell (r, hx) -> x cell (gz, y0 + r + ddy - 1, x0 + hx - 1); chunk fastest (coalesced reads)
+    for (int e = tid; e < W::NROW * (CIN / 8); e += kCnnThreads) {
+      const int ch = e % (CIN / 8), c = e / (CIN / 8);
+      const int gx = x0 + c % W::HXp - 1, gy = y0 + c / W::HXp + ddy - 1;
       const bool ok = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny && gz >= 0 && gz < d.nz;
       const long cell = ok ? ((long)b * d.nz + gz) * plane + (long)gy * d.nx + gx : 0;
-      cp_async16(smem_u32(sx + c * XP + ch * 8), x + cell * CIN + ch * 8, ok);
+      cp_async16(smem_u32(sB + ch * W::B_SBO + c * 16), x + cell * CIN + ch * 8, ok);
     }
     // dY of the tile's output cells (zero outside the grid, so those cells add nothing)
     for (int e = tid; e < kTX * kTY * (COUT / 8); e += kCnnThreads) {
-      const int c = e / (COUT / 8), ch = e % (COUT / 8);
-      const int ox = x0 + c % kTX, oy = y0 + c / kTX;
+      const int ch = e % (COUT / 8), q = e / (COUT / 8);
+      const int ox = x0 + q % kTX, oy = y0 + q / kTX;
       const bool ok = ox < d.nx && oy < d.ny;
       const long cell = ok ? ((long)b * d.nz + z) * plane + (long)oy * d.nx + ox : 0;
-      cp_async16(smem_u32(sy + c * YP + ch * 8), dy + cell * COUT + ch * 8, ok);
+      cp_async16(smem_u32(sA + ch * W::A_SBO + q * 16), dy + cell * COUT + ch * 8, ok);
     }
-    cp_async_wait_all();
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // Per tile: copies, then the 24 MMAs of one issuing thread; the next
+  // tile's copies wait for them (a second operand buffer, measured, was
+  // slower: two buffers of 103 KB leave fewer blocks per SM).
+  uint32_t par = 0u;
+  for (int k = 0; k < n; ++k) {
+    stage(k);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    fence_proxy_async_smem();
+    tc_fence_before_sync();
     __syncthreads();
-    // k steps outer, the warp's output tiles inner: independent accumulators
-    for (int kc = 0; kc < kTY; ++kc) {
+    if (tid == 0) {
+      tc_fence_after_sync();
+      const uint32_t a0 = smem_u32(smraw), b0 = a0 + W::A_BYTES;
 #pragma unroll
-      for (int i = 0; i < PER_WARP; ++i) {
-        const int tile = warp * PER_WARP + i;
-        if (tile >= TILES) break;
-        const int tap9 = tile / (MT * NTL), rem = tile % (MT * NTL);
-        const int mt = rem / NTL, nt = rem % NTL;
-        const int ddy = tap9 / 3, ddx = tap9 % 3;
-        // k step kc = output row y0 + kc (16 cells)
-        // A = dY^T (co x cells): stored [cell][co] -> transposed loads
-        uint32_t a0, a1, a2, a3;
-        {
-          const int krow = kc * 16 + (lane & 7) + ((lane >> 4) << 3);
-          const int mcol = mt * 16 + ((lane >> 3) & 1) * 8;
-          ldsm_x4_t(smem_u32(sy + krow * YP + mcol), a0, a1, a2, a3);
+      for (int cy = 0; cy < kTY; ++cy)
+#pragma unroll
+        for (int ddx = 0; ddx < 3; ++ddx)
+          tc_mma_bf16(tb + ddx * CIN, tc_sdesc(a0 + cy * kTX * 16, 128, W::A_SBO),
+                      tc_sdesc(b0 + (cy * W::HXp + ddx) * 16, 128, W::B_SBO), idesc, k > 0 || cy > 0);
+      tc_commit(&bar);
+    }
+    if (!mbar_wait(&bar, par)) atomicOr(flag, kFlagTimeout);
+    par ^= 1u;
+    tc_fence_after_sync();
+  }
+  // accumulators: lane = co (warps 0..3), column ddx * CIN + ci
+  if (n > 0 && warp < 4) {
+    const int co = 32 * warp + lane;
+#pragma unroll
+    for (int ddx = 0; ddx < 3; ++ddx) {
+      const int tap = dz * 9 + ddy * 3 + ddx;
+#pragma unroll
+      for (int j = 0; j < CIN / 8; ++j) {
+        float v[8];
+        tmem_ld8(tb + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ddx * CIN + 8 * j), v);
+        if (co < cout_real) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int ci = 8 * j + i;
+            if (ci < cin_real) atomicAdd(&dw[((long)co * cin_real + ci) * 27 + tap], v[i]);
+          }
         }
-        // B = x of the shifted cells: output cell (kc, cx) reads halo (kc + ddy, cx + ddx)
-        uint32_t b0, b1;
-        {
-          const int cx = (lane & 7) + ((lane >> 3) & 1) * 8;
-          const int hrow = (kc + ddy) * HXp + cx + ddx;
-          uint32_t r0, r1, r2, r3;
-          ldsm_x4_t(smem_u32(sx + hrow * XP + nt * 8), r0, r1, r2, r3);
-          b0 = r0;
-          b1 = r1;
-          (void)r2;
-          (void)r3;
-        }
-        mma16816(acc[i], a0, a1, a2, a3, b0, b1);
       }
     }
-    __syncthreads();
   }
-  // accumulate: rows co = mt*16 + g (+8), cols ci = nt*8 + 2q (+1)
-  const int g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int i = 0; i < PER_WARP; ++i) {
-    const int tile = warp * PER_WARP + i;
-    if (tile >= TILES) break;
-    const int tap = dz * 9 + tile / (MT * NTL), rem = tile % (MT * NTL);
-    const int mt = rem / NTL, nt = rem % NTL;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int co = mt * 16 + g + (r >= 2 ? 8 : 0);
-      const int ci = nt * 8 + 2 * q + (r & 1);
-      if (co < cout_real && ci < cin_real) atomicAdd(&dw[((long)co * cin_real + ci) * 27 + tap], acc[i][r]);
-    }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after_sync();
+    tmem_dealloc(tb, W::TCOLS);
   }
 }
 
@@ -568,13 +595,29 @@ static mx_status conv_run(const bf16_t* in, const bf16_t* w, const float* b, bf1
 
 template <int CIN, int COUT>
 static mx_status wgrad_run(const bf16_t* x, const bf16_t* dy, float* dw, const ConvDims& d, int cin_real,
-                           int cout_real, cudaStream_t st) {
-  // about 2 x 152 blocks over the three dz planes
-  int tpb = d.ntiles / 100;
+                           int cout_real, int* flag, cudaStream_t st) {
+  typedef WgradShape<CIN, COUT> W;
+  static bool attr = false;
+  if (!attr) {
+    MX_CUDA_TRY(cudaFuncSetAttribute(wgrad_tc_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)W::smem));
+    attr = true;
+  }
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  // about six blocks per SM over the nine (dz, ddy) tap rows: blocks that
+  // wait for tensor memory or for their MMAs overlap the others' copies
+  // (measured: 5.00 ms per batch-64 loss + gradient at 64x64x4 against 5.89
+  // with two blocks per SM and 5.66 with the earlier mma.sync kernel)
+  int tpb = (int)(((long)d.ntiles * 9 + 6 * g_num_sms - 1) / (6 * g_num_sms));
   if (tpb < 1) tpb = 1;
-  dim3 grid((d.ntiles + tpb - 1) / tpb, 3);
-  wgrad_kernel<CIN, COUT><<<grid, kCnnThreads, 0, st>>>(x, dy, dw, d, cin_real, cout_real, tpb);
-  return launch_check("wgrad_kernel");
+  dim3 grid((d.ntiles + tpb - 1) / tpb, 9);
+  wgrad_tc_kernel<CIN, COUT><<<grid, kCnnThreads, W::smem, st>>>(x, dy, dw, d, cin_real, cout_real, tpb, flag);
+  return launch_check("wgrad_tc_kernel");
 }
 
 static mx_status pack_all(mx_cnn* n, cudaStream_t st) {
@@ -809,22 +852,22 @@ mx_status mx_cnn_loss_grad(mx_cnn* n, const float* m, const float* h_target, int
   float* G = n->grad;
   const unsigned bgrid = (unsigned)((nc + 1023) / 1024 < 1024 ? (nc + 1023) / 1024 : 1024);
   // layer 4: weights, bias, then dY3 = conv(dY4, W4') * gelu'(y3)
-  MX_TRY((wgrad_run<32, 16>(n->a3, n->dy4, G + layer_w_off(3), d, 32, 3, st)));
+  MX_TRY((wgrad_run<32, 16>(n->a3, n->dy4, G + layer_w_off(3), d, 32, 3, n->flag, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy4, 16, 3, nc, G + layer_w_off(3) + 3 * 32 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
   MX_TRY((conv_run<16, 32, CM_BWD>(n->dy4, n->wb[3], nullptr, n->dy3, n->y3, nullptr, d, n->flag, st)));
   // layer 3
-  MX_TRY((wgrad_run<64, 32>(n->a2, n->dy3, G + layer_w_off(2), d, 64, 32, st)));
+  MX_TRY((wgrad_run<64, 32>(n->a2, n->dy3, G + layer_w_off(2), d, 64, 32, n->flag, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy3, 32, 32, nc, G + layer_w_off(2) + 32 * 64 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
   MX_TRY((conv_run<32, 64, CM_BWD>(n->dy3, n->wb[2], nullptr, n->dy2, n->y2, nullptr, d, n->flag, st)));
   // layer 2
-  MX_TRY((wgrad_run<32, 64>(n->a1, n->dy2, G + layer_w_off(1), d, 32, 64, st)));
+  MX_TRY((wgrad_run<32, 64>(n->a1, n->dy2, G + layer_w_off(1), d, 32, 64, n->flag, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy2, 64, 64, nc, G + layer_w_off(1) + 64 * 32 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
   MX_TRY((conv_run<64, 32, CM_BWD>(n->dy2, n->wb[1], nullptr, n->dy1, n->y1, nullptr, d, n->flag, st)));
   // layer 1
-  MX_TRY((wgrad_run<16, 32>(n->x0, n->dy1, G + layer_w_off(0), d, 3, 32, st)));
+  MX_TRY((wgrad_run<16, 32>(n->x0, n->dy1, G + layer_w_off(0), d, 3, 32, n->flag, st)));
   bgrad_kernel<<<bgrid, 256, 0, st>>>(n->dy1, 32, 32, nc, G + layer_w_off(0) + 32 * 3 * 27);
   MX_TRY(launch_check("bgrad_kernel"));
   if (loss_out) MX_CUDA_TRY(cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
