@@ -11,13 +11,14 @@
 // tcgen05 tensor cores (BF16 in, FP32 accumulator in tensor memory): a block
 // takes 8 x 16 x 1 tiles of output cells (M = 128) with a (10 x 18 x 3) halo
 // of input cells staged with cp.async; all 27 taps of the layer's weights
-// stay in shared memory.  The weight gradient is a split-K GEMM on
-// mma.sync m16n8k16.
+// stay in shared memory.  The weight gradient runs on tcgen05 too, with
+// MN-major operands (wgrad_tc_kernel).
 //   forward     out = conv(a, W) + b, stored pre-activation y and a = gelu(y)
 //   backward-x  dA_{l-1} = conv(dY_l, W'), W'[tap][ci][co] = W[26 - tap][co][ci],
 //               times gelu'(y_{l-1}) in the epilogue -> dY_{l-1}
 //   backward-W  dW[tap] = sum over cells of dY (x) x_shifted(tap), one block per
-//               (tap, chunk of tiles), FP32 atomics into the gradient
+//               (dz, ddy, chunk of tiles) with its three taps in tensor memory,
+//               FP32 atomics into the gradient
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>

@@ -8,7 +8,11 @@
 // a "core matrix" is 8 rows x 8 elements (8 rows of 16 bytes, 128 contiguous
 // bytes).  Core matrices adjacent along K are LBO bytes apart, 8-row groups
 // adjacent along M (or N) are SBO bytes apart.  One MMA of kind::f16 consumes
-// K = 16 (two core matrices along K).
+// K = 16 (two core matrices along K).  MN-major (instruction-descriptor bits
+// 15 and 16 for A and B): a core matrix is 8 K-rows of 16 bytes, each row 8
+// consecutive M (or N) elements; again LBO is the stride between core
+// matrices adjacent along K and SBO the stride between 8-element groups
+// along M (or N) (settled by a one-MMA check with both readings in bounds).
 #pragma once
 
 #include <stdint.h>
