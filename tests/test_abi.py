@@ -116,3 +116,34 @@ int main(void) {
                     "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.strip().split("|")
     assert "sm_103a" in out[0] and out[1] == "115907" and out[2] == "2368259" and "mx_fno_create" in out[3]
+
+
+def test_schedule_and_mode_enums_match_the_binding(tmp_path):
+    """The demag schedules and FFT modes of mx.h equal the binding's constants."""
+    from paper_2602_12242_gb300 import _lib
+    names = ["MX_DEMAG_AUTO", "MX_DEMAG_GENERIC", "MX_DEMAG_PLANE", "MX_DEMAG_PLANE_PAIR", "MX_DEMAG_PLANE_XLOCAL",
+             "MX_FFT_FP32", "MX_FFT_SPLIT_BF16"]
+    src = tmp_path / "enums.c"
+    src.write_text('#include <stdio.h>\n#include "mx.h"\nint main(void){' +
+                   "".join(f'printf("%d ", (int){n});' for n in names) + "return 0;}")
+    exe = tmp_path / "enums"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [getattr(_lib, n) for n in names]
+
+
+def test_timing_slots_name_the_fused_stage(libmx):
+    """mx_kernel_slot needs no device: every slot has a name, the fused
+    inverse-x + local stage included, and out-of-range slots are empty."""
+    libmx.mx_kernel_slot.restype = ctypes.c_char_p
+    slots = []
+    q = 0
+    while True:
+        s = libmx.mx_kernel_slot(q).decode()
+        if not s:
+            break
+        slots.append(s)
+        q += 1
+    assert {"x_fwd", "yz_fused", "x_inv", "local_stage", "x_inv_local"} <= set(slots)
+    assert libmx.mx_kernel_slot(-1).decode() == ""

@@ -75,3 +75,14 @@ def test_kernel_digest_ignores_comments_and_layout(tmp_path):
     b.write_text("int f(int x) {\n return 2 * x;\n}\n")
     c.write_text("int f(int x) { return 3 * x; }\n")
     assert bench._code_text(str(a)) == bench._code_text(str(b)) != bench._code_text(str(c))
+
+
+def test_algorithmic_bytes_of_the_fused_stage():
+    """The fused inverse-x + local slot counts the spectrum read and the local
+    stage without the H_demag write and read (32 B per cell less than the two
+    separate kernels)."""
+    import bench
+    cfg = {"nx": 512, "ny": 512, "nz": 16}
+    ab = bench.algorithmic_bytes(cfg, (1024, 1024, 32), axis_map=True)
+    nc = 512 * 512 * 16
+    assert ab["x_inv"] + ab["local_stage"] - ab["x_inv_local"] == 32 * nc
