@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import cfg_of, context, random_m
+from helpers import cfg_of, context, problem, random_m, t64
 
 pytestmark = pytest.mark.gpu
 
@@ -105,3 +105,33 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
         _lib.mx_energy_noalloc(p, m, out)
     assert ei.value.status == _lib.MX_ERR_UNSUPPORTED
     assert "limit" in str(ei.value)
+
+
+def test_noalloc_energy_matches_oracle():
+    """mx_energy_noalloc against the FP64 oracle's energies directly (film
+    with DMI and chiral edges, per-cell Ms, Ku and easy axis), the demag field
+    passed in being the library's own H_demag of the same m."""
+    from oracle import micromag as mm
+    from paper_2602_12242_gb300 import MX_TERM_DEMAG, _lib, inputs
+    from paper_2602_12242_gb300.solver import to_dev4
+    c = cfg_of(nx=40, ny=24, nz=1, dx=3.9e-9, dy=3.9e-9, dz=3e-9, D=1.5e-3, dmi=True, Ku=2e4,
+               h_bias=(-2.5e4, 4.3e3, 0.0))
+    shape = (1, 24, 40)
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    Ms = f32(inputs.uniform_map(shape, 6e5, 1e6, 81))
+    Ku = f32(inputs.uniform_map(shape, 1e4, 5e4, 82))
+    axis = f32(inputs.grain_axes(shape, (8, 8, 1), 83))
+    m = f32(random_m(c, 84))
+    ctx = context(c, Ms=Ms, Ku=Ku, axis=axis)
+    md = to_dev4(m)
+    hd = ctx.heff(md, terms=MX_TERM_DEMAG)
+    out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+    _lib.mx_energy_noalloc(_params(ctx), md, out, h_demag=hd,
+                           ms_map=torch.as_tensor(Ms.astype(np.float32)).cuda(),
+                           ku_map=torch.as_tensor(Ku.astype(np.float32)).cuda(), axis_map=to_dev4(axis))
+    torch.cuda.synchronize()
+    got = dict(zip(("demag", "exch", "anis", "dmi", "zeeman"), out.cpu().tolist()))
+    ref = mm.energies(problem(c, Ms=Ms, Ku=Ku, axis=axis), t64(m))
+    scale = sum(abs(v) for v in ref.values())
+    for k in ref:
+        assert abs(got[k] - ref[k]) <= TOL_ENERGY * scale, (k, got[k], ref[k])
